@@ -1,0 +1,295 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, brute force, finite differences, or the one number the
+paper prints (0.0256, App. A.2 / Fig. 6).  A plausible slip in the oracle (a
+dropped term, a wrong sign or index, a transposed operand) fails one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_15401_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def iso_P6(s):
+    v = 1.0 / (s * s)
+    return np.array([v, 0, 0, v, 0, v])
+
+
+def cam_identity(H, W, F):
+    return {"R": np.eye(3), "T": np.zeros(3), "F": F, "Ox": W / 2, "Oy": H / 2, "H": H, "W": W}
+
+
+def random_P6(rng, smin=0.02, smax=0.2):
+    rot = scenes.random_rotations(rng, 1)[0]
+    s = rng.uniform(smin, smax, 3)
+    P = rot @ np.diag(1 / s**2) @ rot.T
+    return np.array([P[0, 0], P[0, 1], P[0, 2], P[1, 1], P[1, 2], P[2, 2]]), P
+
+
+# --------------------------------------------------------------- Eq. 6 ----
+def test_trace_isotropic_closed_form():
+    """P = I/s^2: b = |D|^2/s^2, l = M.D/|D|^2, qt = |M x D|^2 / (|D|^2 s^2)."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        M = rng.normal(0, 1, 3) + np.array([0, 0, 5])
+        D = np.array([rng.normal(0, 0.3), rng.normal(0, 0.3), 1.0])
+        s = rng.uniform(0.01, 0.5)
+        l, qt, b = oracle.trace_dir(M, iso_P6(s), D)
+        d2 = D @ D
+        assert b == pytest.approx(d2 / s**2, rel=1e-12)
+        assert l == pytest.approx(M @ D / d2, rel=1e-12)
+        cr = np.cross(M, D)
+        assert qt == pytest.approx(cr @ cr / (d2 * s**2), rel=1e-9, abs=1e-12)
+
+
+def test_trace_peak_is_argmax_of_density():
+    """App. A.1: l is where the density along the ray peaks, and e^{q} is that peak."""
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        P6, P = random_P6(rng)
+        M = rng.normal(0, 0.5, 3) + np.array([0, 0, 4])
+        D = np.array([rng.normal(0, 0.2), rng.normal(0, 0.2), 1.0])
+        l, qt, b = oracle.trace_dir(M, P6, D)
+
+        def expo(t):  # -2 log density along the ray
+            v = t * D - M
+            return v @ P @ v
+
+        lo, hi = 0.0, 10.0
+        g = (math.sqrt(5) - 1) / 2
+        for _ in range(200):
+            c1, c2 = hi - g * (hi - lo), lo + g * (hi - lo)
+            if expo(c1) < expo(c2):
+                hi = c2
+            else:
+                lo = c1
+        tstar = 0.5 * (lo + hi)
+        assert l == pytest.approx(tstar, abs=1e-6)
+        assert qt == pytest.approx(expo(tstar), rel=1e-8, abs=1e-10)
+        # second derivative of the exponent is 2 DᵀPD = 2b  (1/sigma^2 = DᵀPD)
+        h = 1e-3
+        assert (expo(l + h) - 2 * expo(l) + expo(l - h)) / h**2 == pytest.approx(2 * b, rel=1e-6)
+
+
+def test_trace_direction_scale_invariance():
+    """Scaling D by lam scales l by 1/lam and b by lam^2; qt and u = dl*sqrt(b/2) are unchanged."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        P6a, _ = random_P6(rng)
+        P6b, _ = random_P6(rng)
+        Ma = rng.normal(0, 0.3, 3) + [0, 0, 4]
+        Mb = rng.normal(0, 0.3, 3) + [0, 0, 4.2]
+        D = np.array([rng.normal(0, 0.1), rng.normal(0, 0.1), 1.0])
+        lam = rng.uniform(0.3, 3)
+        la, qa, ba = oracle.trace_dir(Ma, P6a, D)
+        lb, qb, bb = oracle.trace_dir(Mb, P6b, D)
+        la2, qa2, ba2 = oracle.trace_dir(Ma, P6a, lam * D)
+        lb2, qb2, bb2 = oracle.trace_dir(Mb, P6b, lam * D)
+        assert la2 == pytest.approx(la / lam, rel=1e-10)
+        assert ba2 == pytest.approx(ba * lam * lam, rel=1e-10)
+        assert qa2 == pytest.approx(qa, rel=1e-7, abs=1e-10)
+        u1 = (la - lb) * math.sqrt(bb / 2)
+        u2 = (la2 - lb2) * math.sqrt(bb2 / 2)
+        assert u2 == pytest.approx(u1, rel=1e-8, abs=1e-10)
+
+
+# ---------------------------------------------------- Eq. 5 axis reading ----
+def test_ray_axis_convention():
+    """Eq. 5 with pixel centres: a Gaussian at (x, y, z) peaks at column F x/z + Ox - 0.5, row F y/z + Oy - 0.5."""
+    cam = cam_identity(32, 48, 40.0)
+    M = np.array([[0.31, -0.17, 3.0]])
+    r = oracle.render([cam], M, iso_P6(0.05)[None], np.ones((1, 1)), K=0, tau=1.0, eta=0.0)
+    a = r["a"][:, 0].reshape(32, 48)
+    i, j = np.unravel_index(np.argmax(a), a.shape)
+    assert j == round(40 * 0.31 / 3 + 24 - 0.5)
+    assert i == round(40 * -0.17 / 3 + 16 - 0.5)
+    assert j > 24 and i < 16
+
+
+# ---------------------------------------------------------- Eq. 7 / 8 ----
+def test_single_gaussian_transmittance():
+    """One kernel: A = m (erf(0) = 0), so T(l) = exp(-tau a/2) and W = a exp(-tau a/2)."""
+    cam = cam_identity(16, 16, 16.0)
+    s = 0.2
+    M = np.array([[0.05, -0.02, 3.0]])
+    for tau in (0.5, 1.0, 3.0):
+        r = oracle.render([cam], M, iso_P6(s)[None], np.array([[0.7, 0.2, 1.0]]), K=0, tau=tau, eta=0.0)
+        D = np.stack([(r["pix"][:, 2] + 0.5 - 8) / 16, (r["pix"][:, 1] + 0.5 - 8) / 16, np.ones(256)], 1)
+        cr = np.cross(M[0], D)
+        a = np.exp(-0.5 * (cr * cr).sum(1) / ((D * D).sum(1) * s * s))
+        W = a * np.exp(-tau * a / 2)
+        np.testing.assert_allclose(r["weights"][:, 0], W, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(r["image"], W[:, None] * [0.7, 0.2, 1.0], rtol=1e-12, atol=1e-15)
+
+
+def test_two_coincident_gaussians():
+    """Equal l: erf(0) = 0 for both pairs, so T = exp(-tau (m1 + m2)) for both; ties by index."""
+    cam = cam_identity(8, 8, 8.0)
+    M = np.array([[0.0, 0.0, 3.0], [0.0, 0.0, 3.0]])
+    P = np.stack([iso_P6(0.3), iso_P6(0.3)])
+    r = oracle.render([cam], M, P, np.array([[1.0], [2.0]]), K=0, tau=1.0, eta=0.0)
+    a = r["a"]
+    np.testing.assert_array_equal(r["idx"][:, 0], 0)
+    np.testing.assert_array_equal(r["idx"][:, 1], 1)
+    T = np.exp(-(a[:, 0] / 2 + a[:, 1] / 2))
+    np.testing.assert_allclose(r["weights"][:, 0], T * a[:, 0], rtol=1e-12)
+    np.testing.assert_allclose(r["weights"][:, 1], T * a[:, 1], rtol=1e-12)
+
+
+def test_two_separated_gaussians():
+    """l2 - l1 >> sigma: erf -> +-1, so T1 = exp(-tau m1) and T2 = exp(-tau (2 m1 + m2))."""
+    cam = cam_identity(4, 4, 4.0)
+    M = np.array([[0.0, 0.0, 6.0], [0.0, 0.0, 3.0]])  # index 1 is in front
+    P = np.stack([iso_P6(0.05), iso_P6(0.08)])
+    tau = 0.8
+    r = oracle.render([cam], M, P, np.array([[1.0], [1.0]]), K=0, tau=tau, eta=0.0)
+    np.testing.assert_array_equal(r["idx"][:, 0], 1)
+    a_front, a_back = r["a"][:, 0], r["a"][:, 1]
+    np.testing.assert_allclose(r["weights"][:, 0], a_front * np.exp(-tau * a_front / 2), rtol=1e-12)
+    np.testing.assert_allclose(r["weights"][:, 1], a_back * np.exp(-tau * (a_front + a_back / 2)), rtol=1e-12)
+
+
+def test_weights_bounded_and_lists_sorted():
+    sc = scenes.plain_64(seed=4)
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    r = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=0, tau=1.0, eta=0.0)
+    W = r["weights"]
+    assert (W >= 0).all() and (W <= 1).all()
+    for q in range(0, W.shape[0], 97):
+        n = r["count"][q]
+        l = r["l"][q, :n]
+        assert (np.diff(l) >= 0).all()
+        assert (r["idx"][q, n:] == -1).all()
+
+
+def test_gaussian_order_invariance():
+    """Permuting the Gaussians permutes idx and leaves image and weights unchanged."""
+    sc = scenes.plain_64(seed=5, N=40)
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    perm = np.random.default_rng(0).permutation(40)
+    r1 = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=12, tau=1.0, eta=0.02)
+    r2 = oracle.render(cams, sc["means"][perm], sc["inv_cov"][perm], sc["attr"][perm], K=12, tau=1.0, eta=0.02)
+    np.testing.assert_allclose(r1["image"], r2["image"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r1["weights"], r2["weights"], rtol=1e-12, atol=1e-14)
+    mapped = np.where(r2["idx"] >= 0, perm[np.maximum(r2["idx"], 0)], -1)
+    np.testing.assert_array_equal(mapped, r1["idx"])
+
+
+def test_rotation_invariance_of_viewing_transform():
+    """Rotating scene and camera together (M -> Q M, P -> Q P Qᵀ, R -> R Qᵀ) leaves the image unchanged.
+
+    This pins the camera-space inverse covariance to R P Rᵀ (Sec. 3.3, column vectors)."""
+    sc = scenes.plain_64(seed=6, N=30)
+    rng = np.random.default_rng(7)
+    Q = scenes.random_rotations(rng, 1)[0]
+    cam = cam_identity(24, 24, 24.0)
+    cam["R"] = scenes.random_rotations(rng, 1)[0] @ np.eye(3)
+    cam["T"] = np.array([0.1, -0.2, 0.3])
+    # keep the scene in front of the camera: render world = camera frame for cam R
+    means = (cam["R"].T @ (sc["means"].astype(np.float64) - cam["T"]).T).T
+    Pm = np.zeros((30, 3, 3))
+    ix = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for c, (a, b) in enumerate(ix):
+        Pm[:, a, b] = sc["inv_cov"][:, c]
+        Pm[:, b, a] = sc["inv_cov"][:, c]
+    Pw = np.einsum("ia,nab,jb->nij", cam["R"].T, Pm, cam["R"].T)
+    P6 = np.stack([Pw[:, a, b] for a, b in ix], 1)
+    r1 = oracle.render([cam], means, P6, sc["attr"], K=10, tau=1.0, eta=0.01)
+    means2 = means @ Q.T
+    Pw2 = np.einsum("ia,nab,jb->nij", Q, Pw, Q)
+    P62 = np.stack([Pw2[:, a, b] for a, b in ix], 1)
+    cam2 = dict(cam)
+    cam2["R"] = cam["R"] @ Q.T
+    r2 = oracle.render([cam2], means2, P62, sc["attr"], K=10, tau=1.0, eta=0.01)
+    assert r1["weights"].max() > 0.1
+    np.testing.assert_allclose(r2["image"], r1["image"], rtol=1e-9, atol=1e-11)
+    np.testing.assert_array_equal(r2["idx"], r1["idx"])
+
+
+# ----------------------------------------------- App. A.2 / Fig. 6 pin ----
+def test_paper_single_kernel_error_0256():
+    """W - W' = 0.0256 for one kernel through its centre, independent of Sigma and D (Fig. 6)."""
+    gold = json.load(open(GOLDEN))["single_kernel_approximation_error"]
+    for b in (0.5, 3.0, 1e4, 2.5e5):
+        l, a = 4.0, 1.0
+        W_exact = oracle.quad_weights([l], [a], [b], tau=1.0)[0]
+        W_approx = a * math.exp(-0.5 * a)
+        err = W_exact - W_approx
+        # printed to 4 digits
+        assert abs(err - gold["value"]) < 0.5 * 10 ** -gold["printed_digits"] + 1e-12
+        # and the closed form behind it: int T rho = (1 - e^{-tau a}) / tau
+        assert W_exact == pytest.approx((1 - math.exp(-1.0)), abs=1e-11)
+
+
+def test_quadrature_single_kernel_closed_form():
+    """dT/dt = -tau rho T, so the exact single-kernel weight is (1 - e^{-tau a}) / tau for any a, tau, b."""
+    for a, tau, b in [(0.3, 1.0, 10.0), (0.9, 0.5, 400.0), (0.05, 4.0, 1.0), (1.0, 2.0, 9e4)]:
+        W = oracle.quad_weights([2.0], [a], [b], tau)[0]
+        assert W == pytest.approx((1 - math.exp(-tau * a)) / tau, rel=1e-10)
+
+
+def test_quadrature_far_apart_kernels():
+    """Two kernels far apart: the front one sees T = 1 before it, the back one T = e^{-tau a1} in front."""
+    a1, a2, tau = 0.6, 0.8, 1.0
+    W = oracle.quad_weights([3.0, 6.0], [a1, a2], [1e4, 1e4], tau)
+    assert W[0] == pytest.approx((1 - math.exp(-tau * a1)) / tau, rel=1e-9)
+    assert W[1] == pytest.approx(math.exp(-tau * a1) * (1 - math.exp(-tau * a2)) / tau, rel=1e-9)
+
+
+# ------------------------------------------------------- selection -------
+def test_selection_matches_brute_force_sort():
+    """The kept list is exactly the K smallest (l, index) among kernels with a > eta (App. A.3)."""
+    sc = scenes.plain_64(seed=8, N=60)
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    full = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=0, tau=1.0, eta=0.0)
+    for K, eta in [(5, 0.01), (20, 0.001), (3, 0.3)]:
+        r = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=K, tau=1.0, eta=eta)
+        for q in range(0, full["idx"].shape[0], 53):
+            n = full["count"][q]
+            cand = [(full["l"][q, k], full["idx"][q, k]) for k in range(n) if full["a"][q, k] > eta]
+            cand.sort()
+            want = [g for _, g in cand[:K]]
+            got = list(r["idx"][q, : r["count"][q]])
+            assert got == want
+
+
+@pytest.mark.parametrize("name", ["plain_64", "posefit_256"])
+def test_culled_equals_brute_force(name):
+    """Skipping Gaussians outside their exact conic bounding box changes no result."""
+    if name == "plain_64":
+        sc = scenes.plain_64(seed=9)
+        K, eta = 8, 0.01
+    else:
+        sc = scenes.posefit_256(seed=9, N=600, C=4)
+        K, eta = sc["K"], sc["eta"]
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    pix = oracle.all_pixels(cams)
+    if name != "plain_64":
+        pix = pix[::7]
+    a = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=K, tau=1.0, eta=eta, pix=pix, culled=False)
+    b = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=K, tau=1.0, eta=eta, pix=pix, culled=True)
+    assert a["count"].sum() > 0
+    np.testing.assert_array_equal(a["idx"], b["idx"])
+    np.testing.assert_array_equal(a["image"], b["image"])
+
+
+def test_bbox_contains_every_kept_pixel():
+    sc = scenes.plain_64(seed=10)
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    eta = 0.05
+    bb = oracle.bbox(cams, sc["means"], sc["inv_cov"], eta)
+    r = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=0, tau=1.0, eta=eta)
+    pix = r["pix"]
+    for q in range(pix.shape[0]):
+        for k in range(r["count"][q]):
+            g = r["idx"][q, k]
+            x0, x1, y0, y1 = bb[0, g]
+            assert x0 <= pix[q, 2] <= x1 and y0 <= pix[q, 1] <= y1
