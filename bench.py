@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the VoGE renderer hot path on GB300.
+
+One step = one analysis-by-synthesis fitting iteration over 8 views of
+512x512 with N = 50,000 anisotropic Gaussians, K = 20, eta = 0.01, RGB:
+  voge_render_fwd (project, bin, coarse K-nearest selection, fine
+  transmittance/weights/blend) -> voge_mse_grad against the target images ->
+  voge_render_bwd (adjoint, gradients of means, inverse covariances, colours
+  and the 8 camera poses) -> voge_adam_step on all Gaussian parameters.
+Every kernel in the step is this library's.  Metric: Mpix/s (pixels of all
+views rendered forward + backward per second, all ranks).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
+bounded pixel sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s fwd+bwd (50k Gaussians, 512², K=20) vs plain; serving p50/p99 ms"
+UNIT = "Mpix/s"
+WORKLOAD = dict(views=8, side=512, N=50_000, K=20, eta=0.01, C=3, tau=1.0)
+# Algorithmic FP32 work of the fine pass (Eq. 7-8) per (k, j) pair of a pixel's
+# kept list, counting an FMA as 2 FLOP:
+#   forward  24 = depth difference of two-float l (3) + scale (1) + A&S 7.1.28
+#             erf: degree-6 polynomial (12) + 4 squarings (4) + reciprocal (1)
+#             + signed accumulation (3)
+#   backward 52 = the forward pair recomputed (24) + adjoint pair: difference
+#             and scale (4), A&S 7.1.26 erf with e^{-u^2} (15), accumulation of
+#             dm, du, dl_k, dl_j, dr (9)
+# plus, per kept entry, 80 FLOP for the chain to camera space (backward only).
+FLOP_PER_PAIR = {"fwd": 24, "bwd": 52}
+FLOP_PER_ENTRY_BWD = 80
+# GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="voge", choices=["voge", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle ---
+def oracle_sample(sc, cams, n_pix, rng, nthreads):
+    """Oracle forward (brute force over all N) + analytic backward on n_pix sampled pixels."""
+    import oracle
+
+    allp = oracle.all_pixels(cams)
+    pix = np.ascontiguousarray(allp[np.sort(rng.choice(allp.shape[0], n_pix, replace=False))])
+    m, p, a = (sc[k].astype(np.float64) for k in ("means", "inv_cov", "attr"))
+    t0 = time.perf_counter()
+    fwd = oracle.render(cams, m, p, a, K=WORKLOAD["K"], tau=WORKLOAD["tau"], eta=WORKLOAD["eta"], pix=pix,
+                        nthreads=nthreads)
+    g = rng.standard_normal(fwd["image"].shape)
+    oracle.render_bwd(cams, m, p, a, WORKLOAD["tau"], pix, fwd["idx"], g, nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sc, cams, target_s, seed=0):
+    nthreads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    n0 = 16 * nthreads
+    t0 = oracle_sample(sc, cams, n0, rng, nthreads)
+    n = int(min(200_000, max(n0, n0 * target_s / max(t0, 1e-3))))
+    t = oracle_sample(sc, cams, n, rng, nthreads)
+    return {"value": n / t / 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{n} random pixels of the 8x512x512 views, FP64 forward (all {WORKLOAD['N']} Gaussians "
+                      f"tested per pixel) + analytic backward, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2205_15401_gb300 import scenes
+
+    oracle.build()
+    sc = scenes.fit_8x512(seed=args.seed)
+    cams = scenes.cameras(sc, oracle.pose_to_RT)
+    nthreads = os.cpu_count() or 1
+    rng = np.random.default_rng(args.seed)
+    # size each step so that warmup + steps take about two minutes
+    n0 = 8 * nthreads
+    t0 = oracle_sample(sc, cams, n0, rng, nthreads)
+    total = max(1, args.steps + args.warmup)
+    n = int(max(n0, min(100_000, n0 * (120.0 / total) / max(t0, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(sc, cams, n, rng, nthreads)
+    t = 0.0
+    for _ in range(args.steps):
+        t += oracle_sample(sc, cams, n, rng, nthreads)
+    value = n * args.steps / t / 1e6
+    sample = f"{n} random pixels per step of the 8x512x512 views, FP64 forward + analytic backward"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": "fit_8x512 (oracle sample)", **WORKLOAD, "pixels_per_step": n},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# --------------------------------------------------------------- GPU path ---
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2205_15401_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this exact source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == src_hash:
+            try:
+                return float(parts[2])
+            except ValueError:
+                return None
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2205_15401_gb300 import build as vbuild
+    from paper_2205_15401_gb300 import scenes
+    from paper_2205_15401_gb300 import voge
+
+    vbuild.build()
+    voge.lib()
+
+    W = WORKLOAD
+    sc = scenes.fit_8x512(seed=args.seed + rank, N=W["N"], B=W["views"], side=W["side"], C=W["C"], K=W["K"])
+    cams = scenes.cameras(sc, voge.voge_pose_to_RT)
+    N, C = W["N"], W["C"]
+    r = voge.Renderer(cams, N, C, K=W["K"], tau=W["tau"], thresh=W["eta"], device=dev)
+    P = r.pixels
+
+    # flat parameter / gradient / Adam buffers: [means 3N | inv_cov 6N | attr CN]
+    n_par = N * (3 + 6 + C)
+    host_par = np.concatenate([sc["means"].reshape(-1), sc["inv_cov"].reshape(-1), sc["attr"].reshape(-1)])
+    par = torch.tensor(host_par, device=dev)
+    grad = torch.zeros(n_par, device=dev)
+    m_adam, v_adam = torch.zeros(n_par, device=dev), torch.zeros(n_par, device=dev)
+
+    def views(buf):
+        return buf[: 3 * N].view(N, 3), buf[3 * N: 9 * N].view(N, 6), buf[9 * N:].view(N, C)
+
+    means, inv_cov, attr = views(par)
+    g_means, g_inv_cov, g_attr = views(grad)
+    g_cam = torch.zeros((W["views"], 12), device=dev)
+    loss = torch.zeros(1, device=dev)
+    image, weights, index = r.alloc_outputs()
+    g_image = torch.empty_like(image)
+
+    # target: render of the perturbed parameters (outside the timed region)
+    tm = torch.tensor(sc["target_means"], device=dev)
+    ta = torch.tensor(sc["target_attr"], device=dev)
+    target = r.forward(tm, inv_cov.clone(), ta)[0].clone()
+
+    step_no = [0]
+
+    def step():
+        r.forward(means, inv_cov, attr, out=(image, weights, index))
+        loss.zero_()
+        voge.voge_mse_grad(image, target, g_image, loss)
+        r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam, reuse_projection=True)
+        step_no[0] += 1
+        voge.voge_adam_step(par, grad, m_adam, v_adam, lr=1e-4, step=step_no[0])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    voge.voge_trace_reset()
+    voge.voge_trace_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    voge.voge_trace_enable(False)
+    trace = voge.voge_trace_read()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
+    pix_all = torch.tensor([P * args.steps], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pix_all, op=dist.ReduceOp.SUM)
+    ms_max = float(t_max.item())
+    value = float(pix_all.item()) / (ms_max / 1e3) / 1e6
+    launches = sum(n for n, _ in trace.values())
+
+    # ------------------------------------------------ roofline of the top kernel
+    cnt = (index[:, : r.L] >= 0).sum(1).to(torch.float64)
+    pairs = float((cnt * cnt).sum().item())
+    entries = float(cnt.sum().item())
+    top = max(trace.items(), key=lambda kv: kv[1][1]) if trace else (None, (0, 0.0))
+    top_name, (top_n, top_ms) = top
+    roofline = None
+    if top_name and top_n > 0:
+        avg_s = top_ms / top_n / 1e3
+        if top_name.startswith("k_backward"):
+            flop = pairs * FLOP_PER_PAIR["bwd"] + entries * FLOP_PER_ENTRY_BWD
+        elif top_name.startswith("k_render"):
+            flop = pairs * FLOP_PER_PAIR["fwd"]
+        else:
+            flop = None
+        if flop is not None:
+            ach = flop / avg_s / 1e12
+            roofline = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                        "traffic": profiled_traffic(top_name, kernel_source_hash()),
+                        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                        "avg_launch_ms": top_ms / top_n, "pairs_per_launch": pairs}
+    kernels = {k: {"launches": n, "ms_per_launch": t / max(n, 1), "share": t / max(sum(x for _, x in trace.values()),
+                                                                                  1e-30)}
+               for k, (n, t) in trace.items()}
+
+    # ------------------------------------------------ e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_par = torch.tensor(host_par).pin_memory()
+        h_target = target.cpu().pin_memory()
+        h_grad = torch.empty(n_par).pin_memory()
+        h_gcam = torch.empty((W["views"], 12)).pin_memory()
+        h_loss = torch.empty(1).pin_memory()
+
+        def e2e_step():
+            par.copy_(h_par, non_blocking=True)
+            target.copy_(h_target, non_blocking=True)
+            r.forward(means, inv_cov, attr, out=(image, weights, index))
+            loss.zero_()
+            voge.voge_mse_grad(image, target, g_image, loss)
+            grad.zero_()
+            g_cam.zero_()
+            r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam,
+                       reuse_projection=True)
+            h_grad.copy_(grad, non_blocking=True)
+            h_gcam.copy_(g_cam, non_blocking=True)
+            h_loss.copy_(loss, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return float(h_loss[0])
+
+        for _ in range(args.warmup):
+            e2e_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        t_e2e = torch.tensor([time.perf_counter() - t0], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(pix_all.item()) / float(t_e2e.item()) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(4 * (n_par + target.numel())),
+               "d2h_bytes_per_step": int(4 * (n_par + g_cam.numel() + 1)),
+               "ms_per_step": 1e3 * float(t_e2e.item()) / args.steps}
+
+    # ------------------------------------------------ plain comparator
+    plain = None
+    if not args.no_plain:
+        rp = voge.Renderer(cams, N, C, K=W["K"], tau=W["tau"], thresh=W["eta"], flags=voge.VOGE_FLAG_PLAIN,
+                           device=dev)
+
+        def plain_step():
+            rp.forward(means, inv_cov, attr, out=(image, weights, index))
+            loss.zero_()
+            voge.voge_mse_grad(image, target, g_image, loss)
+            rp.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam,
+                        reuse_projection=True)
+            grad.zero_()
+
+        plain_step()
+        torch.cuda.synchronize()
+        k_plain = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k_plain):
+            plain_step()
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / k_plain
+        plain = {"value": P / (pms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": pms,
+                 "what": "same step, every pixel tests every Gaussian (no tile binning)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        cpu = cpu_baseline(sc, scenes.cameras(sc, oracle.pose_to_RT), args.cpu_seconds)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": "fit_8x512: 8 views 512x512, N=50,000 anisotropic Gaussians, K=20, "
+                                      "eta=0.01, RGB; step = forward + MSE + backward + Adam",
+                          **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
+                          "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
+               "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+               "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * voge.h -- C ABI of libvoge.so, the GB300 (sm_103a) implementation of the
+ * VoGE renderer's hot path (Wang et al., "VoGE: A Differentiable Volume
+ * Renderer using Gaussian Ellipsoids for Analysis-by-Synthesis", ICLR 2023).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers marked "device" are CUDA device pointers on the current device;
+ *   pointers marked "host" are ordinary host memory.  The caller owns every
+ *   buffer, including the workspace.  No entry point allocates device memory.
+ * - All device work is enqueued on `stream` (0 = legacy default stream) and
+ *   is asynchronous with respect to the host, except voge_render_fwd /
+ *   voge_render_bwd, which copy the B camera structs from host memory into the
+ *   workspace with cudaMemcpyAsync before their first launch (the host array
+ *   may be reused as soon as the call returns).
+ * - Return value: VOGE_OK (0) or a negative VOGE_ERR_* code; nothing aborts.
+ *   A launch error is reported as VOGE_ERR_CUDA; the CUDA error itself can be
+ *   read with cudaGetLastError() by the caller.
+ * - Camera model (Sec. 3.3 and Eq. 5 of the paper): a Gaussian with world mean
+ *   M_w and world inverse covariance P_w is seen at M = R M_w + T with inverse
+ *   covariance R P_w Rᵀ.  The ray of pixel (row i, column j) is r(t) = tD with
+ *   D = ((j + 0.5 - Ox)/F, (i + 0.5 - Oy)/F, 1): x right, y down, z forward.
+ * - Pixels: views are stored back to back, view v holding H_v x W_v pixels in
+ *   row-major order.  When every view has the same H, W this is [B][H][W].
+ * - Gaussians: means [N][3] (x, y, z); inverse covariances P = Sigma^-1 as six
+ *   floats per Gaussian in the order (xx, xy, xz, yy, yz, zz) of the symmetric
+ *   matrix; attributes [N][C] (RGB when C = 3, or C-channel features).
+ */
+#ifndef VOGE_H
+#define VOGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* voge_stream_t; /* same type as cudaStream_t */
+
+enum {
+    VOGE_OK = 0,
+    VOGE_ERR_ARG = -1,        /* a size, pointer or parameter is invalid */
+    VOGE_ERR_WORKSPACE = -2,  /* workspace NULL or smaller than voge_workspace_bytes() */
+    VOGE_ERR_CUDA = -3,       /* a CUDA call or kernel launch failed */
+    VOGE_ERR_UNSUPPORTED = -4,/* a combination this build does not implement */
+    VOGE_ERR_TIMEOUT = -5,    /* a bounded wait ran out (serving) */
+    VOGE_ERR_ADMISSION = -6,  /* request larger than the server's memory budget */
+    VOGE_ERR_BUSY = -7        /* no free slot / queue full (serving) */
+};
+
+/* One view.  R row-major; M_cam = R M_world + T (Sec. 3.3).  F, Ox, Oy in
+ * pixels (Eq. 5).  H, W: image size of this view. */
+typedef struct {
+    float R[9];
+    float T[3];
+    float F, Ox, Oy;
+    int32_t H, W;
+} voge_camera;
+
+/* Render parameters.
+ *   B       number of views (>= 1)
+ *   N       number of Gaussians (>= 0)
+ *   C       attribute channels (>= 1)
+ *   K       length of each pixel's kept list: the K' nearest kernels of
+ *           Sec. 3.3 / App. A.3.  K <= 0 or K >= N keeps every candidate.
+ *   tau     absorption coefficient of Eq. 1 / Eq. 7 (> 0)
+ *   thresh  eta of App. A.3: a kernel is a candidate for a pixel only if its
+ *           peak density e^{q} on that ray is > thresh.  thresh <= 0: no cut.
+ *   flags   VOGE_FLAG_* bits
+ *   bin_capacity  average number of 16x16 screen tiles per Gaussian that the
+ *           workspace reserves for tile binning (0 = default 8).  Overflow never
+ *           changes a result: the tiles whose lists overflowed fall back to
+ *           testing every Gaussian. */
+typedef struct {
+    int32_t B, N, C, K;
+    float tau, thresh;
+    int32_t flags;
+    int32_t bin_capacity;
+} voge_params;
+
+enum {
+    /* Comparator path: every pixel tests every Gaussian (no tile binning). */
+    VOGE_FLAG_PLAIN = 1,
+    /* voge_render_bwd only: reuse the projection that the matching
+     * voge_render_fwd call left in the same workspace (same cams, params and
+     * Gaussians, workspace untouched in between) instead of recomputing it. */
+    VOGE_FLAG_REUSE_PROJECTION = 2
+};
+
+/* Library version (major*10000 + minor*100 + patch). */
+int voge_version(void);
+
+/* Human-readable text for a VOGE_* code (static storage). */
+const char* voge_strerror(int code);
+
+/* Effective list length: K if 0 < K < N, else N (and 0 when N == 0). */
+int voge_list_length(const voge_params* p);
+
+/* Bytes of device workspace that voge_render_fwd / voge_render_bwd need for
+ * these cameras (host, B entries) and parameters.  Query, allocate, then call.
+ * Returns 0 if the arguments are invalid. */
+size_t voge_workspace_bytes(const voge_camera* cams, const voge_params* p);
+
+/*
+ * Forward render: coarse pass (ray tracing of each ellipsoid, Eq. 6; keep
+ * kernels with e^{q} > thresh and l > 0, sort by peak depth l, keep the K
+ * nearest -- Sec. 3.3, App. A.3) and fine pass (closed-form transmittance of
+ * Eq. 7 over the kept list, weights W_k = T(l_k) e^{q_k} and blend of Eq. 8).
+ *
+ *   cams     host, [B]
+ *   means    device, [N][3] float
+ *   inv_cov  device, [N][6] float (xx, xy, xz, yy, yz, zz of Sigma^-1)
+ *   attr     device, [N][C] float
+ *   image    device, [pixels][C] float, written: sum_k W_k c_k (no background)
+ *   weights  device, [pixels][L] float, written: W_k in list order, 0 padded;
+ *            may be NULL
+ *   index    device, [pixels][L] int32, written: Gaussian index of each kept
+ *            kernel, ascending (l, index), -1 padded.  Required (the backward
+ *            pass reads it).
+ *   L = voge_list_length(p).  Every output element is written.
+ *   workspace  device, >= voge_workspace_bytes(cams, p) bytes, 256-byte aligned.
+ */
+int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                    const float* attr, float* image, float* weights, int32_t* index, void* workspace,
+                    size_t workspace_bytes, voge_stream_t stream);
+
+/*
+ * Backward pass of voge_render_fwd with the kept lists frozen (the selection
+ * is piecewise constant; no gradient flows through it).  Recomputes l, e^{q},
+ * sigma, T(l_k) and every erf term from `index` (nothing else is saved), then
+ * applies the chain rule of Eq. 5-8.
+ *
+ *   index       device, [pixels][L] int32 from voge_render_fwd
+ *   grad_image  device, [pixels][C] float: dLoss/dimage
+ *   grad_means  device, [N][3] float or NULL      -- ACCUMULATED into (+=)
+ *   grad_inv_cov device, [N][6] float or NULL    -- ACCUMULATED; derivative
+ *               with respect to the six stored parameters (so an off-diagonal
+ *               entry receives dL/dP_xy + dL/dP_yx)
+ *   grad_attr   device, [N][C] float or NULL     -- ACCUMULATED
+ *   grad_cam    device, [B][12] float or NULL    -- ACCUMULATED: dL/dR (9,
+ *               row-major) then dL/dT (3) of each view
+ *   The caller zeroes the gradient buffers before the first accumulation.
+ *   Floating-point atomics make the last bits of the gradients depend on
+ *   scheduling.
+ */
+int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                    const float* attr, const int32_t* index, const float* grad_image, float* grad_means,
+                    float* grad_inv_cov, float* grad_attr, float* grad_cam, void* workspace,
+                    size_t workspace_bytes, voge_stream_t stream);
+
+/*
+ * Camera pose (azimuth, elevation, distance, roll), radians -> R, T (host).
+ * Look-at camera: centre dist*(cos e sin a, sin e, cos e cos a), looking at
+ * the world origin, world up +y, then a roll about the optical axis.  The
+ * paper's render-and-compare pose estimation (Sec. 4.1) does not fix a pose
+ * parameterisation; this look-at form is the library's choice.
+ *   pose  host [4];  R host [9] row-major;  T host [3].
+ */
+void voge_pose_to_RT(const double pose[4], float R[9], float T[3]);
+
+/*
+ * Chain rule of voge_pose_to_RT on the device: grad_pose[v] += d(R,T)/d(pose)ᵀ
+ * grad_cam[v] for v < B.
+ *   pose       device [B][4] float
+ *   grad_cam   device [B][12] float (dL/dR row-major, dL/dT), as voge_render_bwd writes
+ *   grad_pose  device [B][4] float, ACCUMULATED
+ */
+int voge_pose_grad(const float* pose, const float* grad_cam, float* grad_pose, int32_t B, voge_stream_t stream);
+
+/*
+ * Mean-squared-error helper for render-and-compare loops (Sec. 4.3 fits a
+ * render to target images): loss[0] += sum((image - target)^2) / n and
+ * grad_image = 2 (image - target) / n, n = count.  All device pointers.
+ */
+int voge_mse_grad(const float* image, const float* target, int64_t count, float* grad_image, float* loss,
+                  voge_stream_t stream);
+
+/*
+ * One Adam step over `count` floats, in place (the optimiser of the paper's
+ * shape fitting, Sec. 4.3):  m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
+ * param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All pointers device, [count] float; step >= 1 is the 1-based step number.
+ * `grad` is set to zero after it is read, ready for the next accumulation by
+ * voge_render_bwd.
+ */
+int voge_adam_step(float* param, float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                   float beta2, float eps, int32_t step, voge_stream_t stream);
+
+/*
+ * Kernel timing (tracing).  While enabled, every kernel launch of the library
+ * is bracketed by two CUDA events on its stream.  voge_trace_read() waits for
+ * the recorded events, adds their device time per kernel name into the
+ * running totals, and copies up to max_entries totals into `out` (host
+ * memory); it returns the number of distinct kernel names seen.
+ * voge_trace_reset() zeroes the totals.  Do not enable while a stream is being
+ * captured into a CUDA graph.  Not part of the paper: an aid for measurement.
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} voge_trace_entry;
+
+int voge_trace_enable(int on); /* returns the previous state */
+int voge_trace_read(voge_trace_entry* out, int max_entries);
+void voge_trace_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOGE_H */

@@ -1,0 +1,367 @@
+// voge_api.cu -- the C ABI of libvoge.so (declared in include/voge.h):
+// argument checks, workspace layout and the launch sequence of one render.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/voge.h"
+#include "voge_device.cuh"
+#include "voge_trace.cuh"
+
+namespace voge {
+cudaError_t launch_project(int64_t BN, int count_tiles, cudaStream_t s, const Args& a);
+cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
+cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
+cudaError_t launch_grad_finalize(int N, cudaStream_t s, const Args& a, float* grad_means, float* grad_inv_cov,
+                                 float* grad_cam);
+}  // namespace voge
+
+using namespace voge;
+
+namespace {
+
+constexpr int kMaxRegisterList = 32;
+
+int list_length(const voge_params* p) {
+    if (p->N <= 0) return 0;
+    return (p->K <= 0 || p->K >= p->N) ? p->N : p->K;
+}
+
+// Register-list capacity and tile height chosen for a list length.
+void pick_variant(int L, int* KM, int* TH) {
+    if (L <= 8) { *KM = 8; *TH = 16; }
+    else if (L <= 16) { *KM = 16; *TH = 16; }
+    else if (L <= 20) { *KM = 20; *TH = 16; }
+    else if (L <= 24) { *KM = 24; *TH = 16; }
+    else if (L <= kMaxRegisterList) { *KM = 32; *TH = 8; }
+    else { *KM = 0; *TH = 16; }  // generic path
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t cams, rec, rec2, tbox, tile_cnt, tile_off, tile_cur, tile_gauss, gcam, gkey, gid, total;
+    int64_t pixels, bin_cap;
+    int32_t total_tiles, TH, KM;
+};
+
+bool valid_params(const voge_camera* cams, const voge_params* p) {
+    if (!cams || !p) return false;
+    if (p->B < 1 || p->N < 0 || p->C < 1) return false;
+    if (!(p->tau > 0.0f) || !isfinite(p->tau) || isnan(p->thresh)) return false;
+    if (p->bin_capacity < 0) return false;
+    for (int v = 0; v < p->B; ++v) {
+        const voge_camera& c = cams[v];
+        if (c.H < 1 || c.W < 1 || !(c.F > 0.0f) || !isfinite(c.F) || !isfinite(c.Ox) || !isfinite(c.Oy)) return false;
+        for (int q = 0; q < 9; ++q)
+            if (!isfinite(c.R[q])) return false;
+        for (int q = 0; q < 3; ++q)
+            if (!isfinite(c.T[q])) return false;
+    }
+    return true;
+}
+
+Layout make_layout(const voge_camera* cams, const voge_params* p) {
+    Layout l;
+    const int L = list_length(p);
+    pick_variant(L, &l.KM, &l.TH);
+    int64_t tiles = 0, pixels = 0;
+    for (int v = 0; v < p->B; ++v) {
+        const int tx = (cams[v].W + kTileW - 1) / kTileW, ty = (cams[v].H + l.TH - 1) / l.TH;
+        tiles += (int64_t)tx * ty;
+        pixels += (int64_t)cams[v].H * cams[v].W;
+    }
+    l.total_tiles = (int32_t)tiles;
+    l.pixels = pixels;
+    const int64_t BN = (int64_t)p->B * p->N;
+    const int cap = p->bin_capacity > 0 ? p->bin_capacity : 8;
+    l.bin_cap = BN * cap;
+    if (l.bin_cap > (int64_t)INT32_MAX) l.bin_cap = INT32_MAX;
+    size_t o = 0;
+    l.cams = o; o = align256(o + sizeof(CamDev) * p->B);
+    l.rec = o; o = align256(o + 64 * (size_t)BN);
+    l.rec2 = o; o = align256(o + 32 * (size_t)BN);
+    l.tbox = o; o = align256(o + 16 * (size_t)BN);
+    l.tile_cnt = o; o = align256(o + 4 * (size_t)(tiles + 1));
+    l.tile_off = o; o = align256(o + 4 * (size_t)(tiles + 1));
+    l.tile_cur = o; o = align256(o + 4 * (size_t)(tiles + 1));
+    l.tile_gauss = o; o = align256(o + 4 * (size_t)l.bin_cap);
+    l.gcam = o; o = align256(o + 36 * (size_t)BN);
+    if (l.KM == 0 && L > 0) {
+        l.gkey = o; o = align256(o + 32 * (size_t)pixels * L);  // 8 floats per entry (backward scratch)
+        l.gid = o; o = align256(o + 4 * (size_t)pixels * L);
+    } else {
+        l.gkey = l.gid = o;
+    }
+    l.total = o + 256;
+    return l;
+}
+
+Ws make_ws(const Layout& l, void* base) {
+    char* b = static_cast<char*>(base);
+    Ws w;
+    w.cams = reinterpret_cast<CamDev*>(b + l.cams);
+    w.rec = reinterpret_cast<float4*>(b + l.rec);
+    w.rec2 = reinterpret_cast<float4*>(b + l.rec2);
+    w.tbox = reinterpret_cast<int4*>(b + l.tbox);
+    w.tile_cnt = reinterpret_cast<int32_t*>(b + l.tile_cnt);
+    w.tile_off = reinterpret_cast<int32_t*>(b + l.tile_off);
+    w.tile_cur = reinterpret_cast<int32_t*>(b + l.tile_cur);
+    w.tile_gauss = reinterpret_cast<int32_t*>(b + l.tile_gauss);
+    w.bin_cap = l.bin_cap;
+    w.gcam = reinterpret_cast<float*>(b + l.gcam);
+    w.gkey = reinterpret_cast<float*>(b + l.gkey);
+    w.gid = reinterpret_cast<int32_t*>(b + l.gid);
+    w.total_tiles = l.total_tiles;
+    return w;
+}
+
+void build_cams(const voge_camera* cams, const voge_params* p, int TH, std::vector<CamDev>& out) {
+    out.resize(p->B);
+    int32_t tile_base = 0;
+    int64_t pix_base = 0;
+    for (int v = 0; v < p->B; ++v) {
+        CamDev& d = out[v];
+        memset(&d, 0, sizeof(d));
+        memcpy(d.R, cams[v].R, sizeof(d.R));
+        memcpy(d.T, cams[v].T, sizeof(d.T));
+        d.F = cams[v].F;
+        d.Ox = cams[v].Ox;
+        d.Oy = cams[v].Oy;
+        d.invF = (float)(1.0 / (double)cams[v].F);
+        d.H = cams[v].H;
+        d.W = cams[v].W;
+        d.tiles_x = (cams[v].W + kTileW - 1) / kTileW;
+        d.tiles_y = (cams[v].H + TH - 1) / TH;
+        d.tile_h = TH;
+        d.tile_base = tile_base;
+        d.pix_base = pix_base;
+        tile_base += d.tiles_x * d.tiles_y;
+        pix_base += (int64_t)cams[v].H * cams[v].W;
+    }
+}
+
+Args make_args(const voge_params* p, const Layout& l, void* ws) {
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.B = p->B;
+    a.N = p->N;
+    a.C = p->C;
+    a.K = p->K;
+    a.L = list_length(p);
+    a.tau = p->tau;
+    a.use_thresh = p->thresh > 0.0f ? 1 : 0;
+    a.Qeta = a.use_thresh ? (p->thresh >= 1.0f ? 0.0f : (float)(2.0 * log(1.0 / (double)p->thresh))) : INFINITY;
+    a.plain = (p->flags & VOGE_FLAG_PLAIN) ? 1 : 0;
+    a.ws = make_ws(l, ws);
+    return a;
+}
+
+// Upload cameras and project every (view, Gaussian); with `bin` also build
+// the tile lists.
+int project_and_bin(const voge_camera* cams, const voge_params* p, const Layout& l, const Args& a, int bin,
+                    cudaStream_t s) {
+    std::vector<CamDev> cd;
+    build_cams(cams, p, l.TH, cd);
+    if (cudaMemcpyAsync(a.ws.cams, cd.data(), sizeof(CamDev) * p->B, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return VOGE_ERR_CUDA;
+    const int64_t BN = (int64_t)p->B * p->N;
+    const int count_tiles = bin && !a.plain;
+    if (count_tiles && cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(l.total_tiles + 1), s) != cudaSuccess)
+        return VOGE_ERR_CUDA;
+    return launch_project(BN, count_tiles, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+__global__ void k_pose_grad(const float* pose, const float* gcam, float* gpose, int B) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= B) return;
+    const float az = pose[4 * v], el = pose[4 * v + 1], ro = pose[4 * v + 3];
+    float sa, ca, se, ce, sr, cr;
+    sincosf(az, &sa, &ca);
+    sincosf(el, &se, &ce);
+    sincosf(ro, &sr, &cr);
+    // R = Rz(roll) R0(az, el), rows of R0: right, down, forward; T = (0, 0, dist)
+    const float rt[3] = {ca, 0.f, -sa}, dn[3] = {se * sa, -ce, se * ca};
+    const float drt_a[3] = {-sa, 0.f, -ca};
+    const float ddn_a[3] = {se * ca, 0.f, -se * sa}, ddn_e[3] = {ce * sa, se, ce * ca};
+    const float dfw_a[3] = {-ce * ca, 0.f, ce * sa}, dfw_e[3] = {se * sa, -ce, se * ca};
+    const float* g = gcam + 12 * v;
+    float ga = 0.f, ge = 0.f, gr = 0.f;
+    for (int q = 0; q < 3; ++q) {
+        // row0 = cr rt - sr dn ; row1 = sr rt + cr dn ; row2 = fw
+        ga += g[q] * (cr * drt_a[q] - sr * ddn_a[q]) + g[3 + q] * (sr * drt_a[q] + cr * ddn_a[q]) + g[6 + q] * dfw_a[q];
+        ge += g[q] * (-sr * ddn_e[q]) + g[3 + q] * (cr * ddn_e[q]) + g[6 + q] * dfw_e[q];
+        gr += g[q] * (-sr * rt[q] - cr * dn[q]) + g[3 + q] * (cr * rt[q] - sr * dn[q]);
+    }
+    gpose[4 * v + 0] += ga;
+    gpose[4 * v + 1] += ge;
+    gpose[4 * v + 2] += g[11];
+    gpose[4 * v + 3] += gr;
+}
+
+__global__ void __launch_bounds__(256) k_mse(const float* x, const float* y, int64_t n, float* gx, float* loss) {
+    __shared__ float red[8];
+    const float inv = 1.0f / (float)n;
+    float acc = 0.0f;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const float d = x[q] - y[q];
+        acc = fmaf(d, d, acc);
+        gx[q] = 2.0f * d * inv;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(loss, s * inv);
+    }
+}
+
+// One Adam step (Kingma & Ba 2015) over n parameters, bias-corrected with
+// the 1-based step count; the gradient is zeroed once read.
+__global__ void __launch_bounds__(256) k_adam(float* x, float* g, float* m, float* v, int64_t n, float lr,
+                                              float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const float gq = g[q];
+        g[q] = 0.0f;  // consumed: ready for the next accumulation
+        const float mq = fmaf(b1, m[q] - gq, gq);
+        const float vq = fmaf(b2, v[q] - gq * gq, gq * gq);
+        m[q] = mq;
+        v[q] = vq;
+        x[q] -= lr * (mq * c1) / (sqrtf(vq * c2) + eps);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int voge_version(void) { return 100; }
+
+const char* voge_strerror(int code) {
+    switch (code) {
+        case VOGE_OK: return "ok";
+        case VOGE_ERR_ARG: return "invalid argument";
+        case VOGE_ERR_WORKSPACE: return "workspace missing or too small";
+        case VOGE_ERR_CUDA: return "CUDA call or kernel launch failed";
+        case VOGE_ERR_UNSUPPORTED: return "unsupported combination";
+        case VOGE_ERR_TIMEOUT: return "bounded wait ran out";
+        case VOGE_ERR_ADMISSION: return "request exceeds the memory budget";
+        case VOGE_ERR_BUSY: return "no free slot";
+        default: return "unknown error";
+    }
+}
+
+int voge_list_length(const voge_params* p) { return p ? list_length(p) : 0; }
+
+size_t voge_workspace_bytes(const voge_camera* cams, const voge_params* p) {
+    if (!valid_params(cams, p)) return 0;
+    return make_layout(cams, p).total;
+}
+
+int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                    const float* attr, float* image, float* weights, int32_t* index, void* workspace,
+                    size_t workspace_bytes, voge_stream_t stream_) {
+    if (!valid_params(cams, p) || !image) return VOGE_ERR_ARG;
+    if (p->N > 0 && (!means || !inv_cov || !attr || !index)) return VOGE_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    const Layout l = make_layout(cams, p);
+    if (!workspace || workspace_bytes < l.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return VOGE_ERR_WORKSPACE;
+    if (p->N == 0) {
+        return cudaMemsetAsync(image, 0, sizeof(float) * (size_t)l.pixels * p->C, s) == cudaSuccess ? VOGE_OK
+                                                                                                    : VOGE_ERR_CUDA;
+    }
+    Args a = make_args(p, l, workspace);
+    a.means = means;
+    a.inv_cov = inv_cov;
+    a.attr = attr;
+    a.image = image;
+    a.weights = weights;
+    a.index = index;
+    int rc = project_and_bin(cams, p, l, a, 1, s);
+    if (rc != VOGE_OK) return rc;
+    if (l.total_tiles == 0) return VOGE_OK;
+    return launch_render_tiles(l.KM, l.total_tiles, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                    const float* attr, const int32_t* index, const float* grad_image, float* grad_means,
+                    float* grad_inv_cov, float* grad_attr, float* grad_cam, void* workspace, size_t workspace_bytes,
+                    voge_stream_t stream_) {
+    if (!valid_params(cams, p) || !grad_image) return VOGE_ERR_ARG;
+    if (p->N == 0) return VOGE_OK;
+    if (!means || !inv_cov || !attr || !index) return VOGE_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    const Layout l = make_layout(cams, p);
+    if (!workspace || workspace_bytes < l.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return VOGE_ERR_WORKSPACE;
+    Args a = make_args(p, l, workspace);
+    a.means = means;
+    a.inv_cov = inv_cov;
+    a.attr = attr;
+    a.index_in = index;
+    a.grad_image = grad_image;
+    a.grad_attr = grad_attr;
+    if (!(p->flags & VOGE_FLAG_REUSE_PROJECTION)) {
+        int rc = project_and_bin(cams, p, l, a, 0, s);
+        if (rc != VOGE_OK) return rc;
+    }
+    const bool geo = grad_means || grad_inv_cov || grad_cam;
+    if (cudaMemsetAsync(a.ws.gcam, 0, 36 * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
+    if (l.total_tiles > 0 && launch_backward_tiles(l.KM, l.total_tiles, s, a) != cudaSuccess) return VOGE_ERR_CUDA;
+    if (geo && launch_grad_finalize(p->N, s, a, grad_means, grad_inv_cov, grad_cam) != cudaSuccess)
+        return VOGE_ERR_CUDA;
+    return VOGE_OK;
+}
+
+void voge_pose_to_RT(const double pose[4], float R[9], float T[3]) {
+    const double sa = sin(pose[0]), ca = cos(pose[0]), se = sin(pose[1]), ce = cos(pose[1]);
+    const double sr = sin(pose[3]), cr = cos(pose[3]);
+    const double rt[3] = {ca, 0.0, -sa}, dn[3] = {se * sa, -ce, se * ca}, fw[3] = {-ce * sa, -se, -ce * ca};
+    for (int q = 0; q < 3; ++q) {
+        R[q] = (float)(cr * rt[q] - sr * dn[q]);
+        R[3 + q] = (float)(sr * rt[q] + cr * dn[q]);
+        R[6 + q] = (float)fw[q];
+    }
+    T[0] = 0.0f;
+    T[1] = 0.0f;
+    T[2] = (float)pose[2];
+}
+
+int voge_pose_grad(const float* pose, const float* grad_cam, float* grad_pose, int32_t B, voge_stream_t stream_) {
+    if (B < 0 || (B > 0 && (!pose || !grad_cam || !grad_pose))) return VOGE_ERR_ARG;
+    if (B == 0) return VOGE_OK;
+    TraceScope tr("k_pose_grad", reinterpret_cast<cudaStream_t>(stream_));
+    k_pose_grad<<<(B + 127) / 128, 128, 0, reinterpret_cast<cudaStream_t>(stream_)>>>(pose, grad_cam, grad_pose, B);
+    return cudaPeekAtLastError() == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+int voge_mse_grad(const float* image, const float* target, int64_t count, float* grad_image, float* loss,
+                  voge_stream_t stream_) {
+    if (count < 0 || (count > 0 && (!image || !target || !grad_image || !loss))) return VOGE_ERR_ARG;
+    if (count == 0) return VOGE_OK;
+    int64_t nb = (count + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    TraceScope tr("k_mse", reinterpret_cast<cudaStream_t>(stream_));
+    k_mse<<<(unsigned)nb, 256, 0, reinterpret_cast<cudaStream_t>(stream_)>>>(image, target, count, grad_image, loss);
+    return cudaPeekAtLastError() == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+int voge_adam_step(float* param, float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                   float beta2, float eps, int32_t step, voge_stream_t stream_) {
+    if (count < 0 || step < 1 || (count > 0 && (!param || !grad || !m || !v))) return VOGE_ERR_ARG;
+    if (count == 0) return VOGE_OK;
+    const float c1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
+    const float c2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
+    int64_t nb = (count + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    TraceScope tr("k_adam", s);
+    k_adam<<<(unsigned)nb, 256, 0, s>>>(param, grad, m, v, count, lr, beta1, beta2, eps, c1, c2);
+    return cudaPeekAtLastError() == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// voge_device.cuh -- device-side types and helpers of libvoge (sm_103a).
+//
+// Geometry of one Gaussian seen from one view (Eq. 6 of the paper, rewritten
+// around the ray through the Gaussian's centre so that FP32 keeps the
+// precision the FP64 reference has):
+//
+//   M = (Mx, My, Mz) camera-space mean, P camera-space inverse covariance,
+//   Mh = M / Mz = (xh, yh, 1) its centre ray, D = Mh + D' with
+//   D' = (du/F, dv/F, 0), (du, dv) = pixel-centre offset from the projected
+//   centre (uc, vc) = (F xh + Ox, F yh + Oy).
+//
+//   b   = DᵀPD               = beta0 + 2 lin + quad
+//   lin = Mhᵀ P D'            = beta1 du + beta2 dv
+//   quad= D'ᵀ P D'            = g00 du^2 + 2 g01 du dv + g11 dv^2
+//   l   = MᵀPD / b            = Mz - Mz (quad + lin) / b        (peak depth)
+//   qt  = (M - lD)ᵀP(M - lD)  = Mz^2 (M x D')ᵀ adj(P) (M x D') / (Mz^2 b)
+//                             = (q00 du^2 + 2 q01 du dv + q11 dv^2) / b
+//   a   = e^{q} = exp(-qt/2), sigma^2 = 1/b.
+//
+// The qt form is the Lagrange identity (MᵀPM)(DᵀPD) - (MᵀPD)^2 =
+// (M x D)ᵀ adj(P) (M x D): it has no cancellation, unlike MᵀPM - (MᵀPD)^2/b.
+// The depth l is kept as two floats (Mz_hi, Mz_lo + dl) so that l_k - l_j in
+// the erf argument of Eq. 7 is exact to FP32 rounding of the difference.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace voge {
+
+constexpr int kTileW = 16;     // tile width in pixels (one warp covers 16 x 2 pixels)
+constexpr int kSortMax = 2048; // tiles with more candidates are processed unsorted
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-view camera as the kernels read it (built on the host from voge_camera).
+struct CamDev {
+    float R[9];
+    float T[3];
+    float F, Ox, Oy, invF;
+    int32_t H, W, tiles_x, tiles_y;
+    int32_t tile_base;  // first global tile id of this view
+    int32_t tile_h;     // tile height in pixels
+    int32_t pad0, pad1;
+    int64_t pix_base;   // first global pixel id of this view
+    int64_t pad2;
+};
+static_assert(sizeof(CamDev) == 112, "CamDev layout");
+
+// Projected record of one (view, Gaussian): 4 x float4 = 64 bytes.
+//   r0 = (uc_hi, uc_lo, vc_hi, vc_lo)   centre, pixel units (u = column + 0.5)
+//   r1 = (beta0, beta1, beta2, g00)
+//   r2 = (2 g01, g11, q00, 2 q01)
+//   r3 = (q11, Mz_hi, Mz_lo, lmin)      lmin: lower bound of l over the pixels
+//                                       where the Gaussian is a candidate
+// An invalid Gaussian (behind the camera, non-finite) has r1 = r2 = 0 so that
+// b = 0 and it never passes the b > 0 test.
+// Second record (backward only): 2 x float4 = (Pxx, Pxy, Pxz, Pyy), (Pyz, Pzz, xh, yh).
+
+// ------------------------------------------------------------------------
+// Hardware approximations (PTX ISA: ex2.approx, rcp.approx).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// erfc(x) for x >= 0 by Abramowitz & Stegun (1964), eq. 7.1.28:
+//   erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16,  |error| <= 3e-7.
+// Returns the (...)^-16 term.  For large x the power overflows to +inf and
+// the reciprocal is 0, i.e. erf = 1.
+__device__ __forceinline__ float erfc_as28(float x) {
+    float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
+    p = fmaf(p, x, 1.520143e-4f);
+    p = fmaf(p, x, 9.2705272e-3f);
+    p = fmaf(p, x, 4.22820123e-2f);
+    p = fmaf(p, x, 7.05230784e-2f);
+    p = fmaf(p, x, 1.0f);
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    return rcp_approx(p);
+}
+
+// erfc(x) for x >= 0 by Abramowitz & Stegun (1964), eq. 7.1.26:
+//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
+//   t = 1 / (1 + p x),  |error| <= 1.5e-7.
+// Also returns g = e^{-x^2}, which the backward pass needs for d erf/dx.
+__device__ __forceinline__ float erfc_as26(float x, float& g) {
+    float t = rcp_approx(fmaf(0.3275911f, x, 1.0f));
+    float s = fmaf(t, 1.061405429f, -1.453152027f);
+    s = fmaf(s, t, 1.421413741f);
+    s = fmaf(s, t, -0.284496736f);
+    s = fmaf(s, t, 0.254829592f);
+    s = s * t;
+    g = ex2_approx(x * (x * -kLog2e));
+    return s * g;
+}
+
+// ------------------------------------------------------------------------
+// Double-float (unevaluated sum of two floats) helpers for the camera
+// transform and the projected centre.
+// ------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+    float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    dfl s = two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ dfl df_mul_f(dfl x, float y) {
+    dfl p = two_prod(x.hi, y);
+    float e = fmaf(x.lo, y, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dfl df_div(dfl x, dfl y) {
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    dfl p = two_prod(q1, y.hi);
+    float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo), __fmul_rn(q1, y.lo));
+    float q2 = __fdiv_rn(r, y.hi);
+    return fast_two_sum(q1, q2);
+}
+// exact-ish a.x + b.y + c.z + d with a, x... floats
+__device__ __forceinline__ dfl df_dot3_add(float a0, float x0, float a1, float x1, float a2, float x2, float d) {
+    dfl s = two_prod(a0, x0);
+    s = df_add(s, two_prod(a1, x1));
+    s = df_add(s, two_prod(a2, x2));
+    return df_add(s, dfl{d, 0.0f});
+}
+
+// ------------------------------------------------------------------------
+// Per-pixel trace of one Gaussian from its record (Eq. 6).
+// ------------------------------------------------------------------------
+struct Trace {
+    float du, dv, b, num, qb;
+};
+
+__device__ __forceinline__ Trace trace_px(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                          float px, float py) {
+    Trace t;
+    t.du = __fsub_rn(__fsub_rn(px, r0.x), r0.y);
+    t.dv = __fsub_rn(__fsub_rn(py, r0.z), r0.w);
+    float dv2 = t.dv * t.dv;
+    float lin = fmaf(r1.y, t.du, r1.z * t.dv);
+    float quad = fmaf(t.du, fmaf(r1.w, t.du, r2.x * t.dv), r2.y * dv2);
+    t.num = quad + lin;
+    t.b = (r1.x + lin) + t.num;
+    t.qb = fmaf(t.du, fmaf(r2.z, t.du, r2.w * t.dv), r3.x * dv2);
+    return t;
+}
+
+// Candidate test of App. A.3 (e^{q} > eta, i.e. qt < Qeta = 2 ln(1/eta)) plus
+// b > 0 and l > 0; returns the sort key l (> 0) or 0 when rejected.
+__device__ __forceinline__ float candidate_key(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                               float px, float py, float Qeta) {
+    Trace t = trace_px(r0, r1, r2, r3, px, py);
+    if (!(t.b > 0.0f) || !(t.qb < Qeta * t.b)) return 0.0f;
+    float dl = -r3.y * t.num * rcp_approx(t.b);
+    float l = r3.y + (r3.z + dl);
+    return l > 0.0f ? l : 0.0f;
+}
+
+// Fine-pass values of a kept Gaussian: l = hi + lo, r = sqrt(b/2) = 1/(sqrt2 sigma), a = e^{q}.
+struct Entry {
+    float hi, lo, r, a;
+};
+__device__ __forceinline__ Entry entry_px(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                          float px, float py) {
+    Trace t = trace_px(r0, r1, r2, r3, px, py);
+    float ib = rcp_approx(t.b);
+    Entry e;
+    e.hi = r3.y;
+    e.lo = r3.z - r3.y * t.num * ib;
+    e.r = sqrtf(0.5f * t.b);
+    e.a = ex2_approx(-0.5f * kLog2e * t.qb * ib);
+    return e;
+}
+
+__device__ __forceinline__ void load_rec(const float4* __restrict__ rec, int64_t o, float4& r0, float4& r1,
+                                         float4& r2, float4& r3) {
+    r0 = __ldg(rec + 4 * o + 0);
+    r1 = __ldg(rec + 4 * o + 1);
+    r2 = __ldg(rec + 4 * o + 2);
+    r3 = __ldg(rec + 4 * o + 3);
+}
+
+// Sorted insertion into a register list of KM (key, id) pairs, ascending by
+// (key, id).  The caller has checked that (l, g) beats the last entry.
+template <int KM>
+__device__ __forceinline__ void topk_insert(float (&key)[KM], int32_t (&id)[KM], float l, int32_t g) {
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        bool lt = (l < key[s]) || (l == key[s] && g < id[s]);
+        float tk = lt ? key[s] : l;
+        int32_t ti = lt ? id[s] : g;
+        key[s] = lt ? l : key[s];
+        id[s] = lt ? g : id[s];
+        l = tk;
+        g = ti;
+    }
+}
+
+__device__ __forceinline__ int find_view(const CamDev* __restrict__ cams, int B, int tile) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&cams[mid].tile_base) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Workspace views shared by the launches of one render call.
+struct Ws {
+    CamDev* cams;
+    float4* rec;      // [B*N][4]
+    float4* rec2;     // [B*N][2]
+    int4* tbox;       // [B*N]: tile range tx0, tx1, ty0, ty1 (tx0 > tx1: none)
+    int32_t* tile_cnt;
+    int32_t* tile_off;
+    int32_t* tile_cur;
+    int32_t* tile_gauss;
+    int64_t bin_cap;
+    float* gcam;      // [B*N][9] backward accumulators (dM 3, G 6)
+    float* gkey;      // [pixels][L] generic path lists
+    int32_t* gid;
+    int32_t total_tiles;
+};
+
+struct Args {
+    int32_t B, N, C, K, L;  // K: requested, L: list length
+    float tau, Qeta;
+    int32_t use_thresh, plain;
+    const float* means;
+    const float* inv_cov;
+    const float* attr;
+    float* image;
+    float* weights;
+    int32_t* index;
+    const int32_t* index_in;
+    const float* grad_image;
+    float* grad_attr;
+    Ws ws;
+};
+
+}  // namespace voge

@@ -1,0 +1,386 @@
+// voge_forward.cu -- fused coarse + fine forward pass, one CTA per tile of
+// 16 x TH pixels, one thread per pixel.
+//
+// Coarse pass (Sec. 3.3, App. A.3): the tile's candidate Gaussians are staged
+// in shared memory in chunks; every pixel traces each of them (Eq. 6), keeps
+// those with e^{q} > eta and l > 0, and holds the K nearest by (l, index) in
+// a register list.  When eta > 0 the candidates are first sorted by a lower
+// bound of l, so a pixel stops as soon as no later candidate can enter.
+//
+// Fine pass (Eq. 7-8): with the kept list L_p,
+//   A_k = sum_{j in L_p} (a_j/2)(1 + erf((l_k - l_j) sqrt(b_j/2))),
+//   T_k = exp(-tau A_k),  W_k = T_k a_k,  image = sum_k W_k c_k.
+// The list's (l, r, a/2) are streamed from shared memory over j while the k
+// side stays in registers; erf is Abramowitz & Stegun 7.1.28 on the FMA pipe
+// plus one MUFU reciprocal.
+#include "voge_device.cuh"
+#include "voge_trace.cuh"
+
+namespace voge {
+
+// Bitonic sort of (key, id) pairs in shared memory, ascending by key.
+template <int NT>
+__device__ void bitonic_sort(float* key, int32_t* id, int n_pow2) {
+    for (int k = 2; k <= n_pow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = threadIdx.x; x < n_pow2; x += NT) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const bool up = (x & k) == 0;
+                    const float kx = key[x], ky = key[y];
+                    if ((kx > ky) == up) {
+                        key[x] = ky;
+                        key[y] = kx;
+                        const int32_t t = id[x];
+                        id[x] = id[y];
+                        id[y] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Candidate source of one tile.
+struct TileSrc {
+    int mode;          // 0 = binned list in global, 1 = sorted list in smem, 2 = every Gaussian (plain/overflow)
+    int filter_box;    // mode 2: test the Gaussian's tile box
+    int count;
+    int start;
+};
+
+template <int NT>
+__device__ __forceinline__ TileSrc tile_source(const Args& a, int t, int tx, int ty, int v, float* s_key,
+                                               int32_t* s_id) {
+    TileSrc src;
+    src.filter_box = 0;
+    if (a.plain) {
+        src.mode = 2;
+        src.count = a.N;
+        src.start = 0;
+        return src;
+    }
+    const int cnt = a.ws.tile_cnt[t];
+    const int off = a.ws.tile_off[t];
+    if ((int64_t)off + cnt > a.ws.bin_cap) {  // binning overflowed: test every Gaussian against its box
+        src.mode = 2;
+        src.filter_box = 1;
+        src.count = a.N;
+        src.start = 0;
+        return src;
+    }
+    src.count = cnt;
+    src.start = off;
+    if (a.use_thresh && cnt > 1 && cnt <= kSortMax) {
+        int n2 = 1;
+        while (n2 < cnt) n2 <<= 1;
+        const int64_t vb = (int64_t)v * a.N;
+        for (int x = threadIdx.x; x < n2; x += NT) {
+            if (x < cnt) {
+                const int32_t g = a.ws.tile_gauss[off + x];
+                s_key[x] = __ldg(&a.ws.rec[4 * (vb + g) + 3].w);
+                s_id[x] = g;
+            } else {
+                s_key[x] = INFINITY;
+                s_id[x] = -1;
+            }
+        }
+        __syncthreads();
+        bitonic_sort<NT>(s_key, s_id, n2);
+        src.mode = 1;
+    } else {
+        src.mode = 0;
+    }
+    return src;
+}
+
+template <int KM, int TH>
+__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
+    constexpr int NT = 16 * TH;
+    extern __shared__ float4 smem[];
+    // phase 1 layout: stage[4][NT] float4 | sgid[NT] | skey[kSortMax] | sid[kSortMax]
+    float4* stage = smem;
+    int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
+    float* skey = reinterpret_cast<float*>(sgid + NT);
+    int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
+    // phase 2 layout: jst[KM][NT] float4 (aliases phase 1)
+    float4* jst = smem;
+
+    const CamDev* cams = a.ws.cams;
+    const int t = blockIdx.x;
+    const int v = find_view(cams, a.B, t);
+    const int lt = t - __ldg(&cams[v].tile_base);
+    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int tx = lt % tiles_x, ty = lt / tiles_x;
+    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
+    const int tid = threadIdx.x;
+    const int j = tx * kTileW + (tid & 15);
+    const int i = ty * TH + (tid >> 4);
+    const bool valid = (i < H) && (j < W);
+    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
+    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
+    const int64_t vb = (int64_t)v * a.N;
+    const int K = a.L;  // list length (<= KM)
+
+    float key[KM];
+    int32_t id[KM];
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        key[s] = (s < KM - K) ? -INFINITY : INFINITY;
+        id[s] = -1;
+    }
+
+    const TileSrc src = tile_source<NT>(a, t, tx, ty, v, skey, sid);
+    bool active = valid;
+    for (int base = 0; base < src.count; base += NT) {
+        const int nc = min(NT, src.count - base);
+        if (tid < nc) {
+            int32_t g;
+            if (src.mode == 1) g = sid[base + tid];
+            else if (src.mode == 0) g = a.ws.tile_gauss[src.start + base + tid];
+            else g = base + tid;
+            float4 r0, r1, r2, r3;
+            load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+            if (src.filter_box) {
+                const int4 tb = a.ws.tbox[vb + g];
+                if (tx < tb.x || tx > tb.y || ty < tb.z || ty > tb.w) {
+                    r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    r2 = r1;
+                }
+            }
+            stage[0 * NT + tid] = r0;
+            stage[1 * NT + tid] = r1;
+            stage[2 * NT + tid] = r2;
+            stage[3 * NT + tid] = r3;
+            sgid[tid] = g;
+        }
+        __syncthreads();
+        if (active) {
+            for (int q = 0; q < nc; ++q) {
+                const float4 r3 = stage[3 * NT + q];
+                if (src.mode == 1 && r3.w > key[KM - 1]) {
+                    active = false;  // sorted by lower bound: nothing later can enter
+                    break;
+                }
+                const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q];
+                const float l = candidate_key(r0, r1, r2, r3, px, py, a.Qeta);
+                if (l > 0.0f) {
+                    const int32_t g = sgid[q];
+                    if (l < key[KM - 1] || (l == key[KM - 1] && g < id[KM - 1])) topk_insert<KM>(key, id, l, g);
+                }
+            }
+        }
+        if (__syncthreads_and(!active)) break;
+    }
+    __syncthreads();  // staging area becomes the j-stream
+
+    // ---------------- fine pass ----------------
+    float hi[KM], lo[KM], A[KM];
+    int n = 0;
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        hi[s] = 0.0f;
+        lo[s] = 0.0f;
+        A[s] = 0.0f;
+        if (valid && s >= KM - K && key[s] < INFINITY) {
+            float4 r0, r1, r2, r3;
+            load_rec(a.ws.rec, vb + id[s], r0, r1, r2, r3);
+            const Entry e = entry_px(r0, r1, r2, r3, px, py);
+            hi[s] = e.hi;
+            lo[s] = e.lo;
+            jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
+            ++n;
+        }
+    }
+    for (int e = 0; e < n; ++e) {
+        const float4 J = jst[e * NT + tid];
+#pragma unroll
+        for (int s = 0; s < KM; ++s) {
+            const float u = ((hi[s] - J.x) + (lo[s] - J.y)) * J.z;
+            const float q = erfc_as28(fabsf(u));
+            const float sm = copysignf(J.w, u);
+            A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
+        }
+    }
+    if (!valid) return;
+
+    const float ntl = -a.tau * kLog2e;
+    float Wt[KM];
+    int e = 0;
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        Wt[s] = 0.0f;
+        if (s >= KM - K && key[s] < INFINITY) {
+            const float am = jst[e * NT + tid].w;
+            Wt[s] = ex2_approx(ntl * A[s]) * (2.0f * am);
+            ++e;
+        }
+    }
+    // outputs: weights / index in list order, image = sum W_k c_k
+    const int L = a.L;
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        if (s >= KM - K) {
+            const int k = s - (KM - K);
+            const bool real = key[s] < INFINITY;
+            a.index[pix * L + k] = real ? id[s] : -1;
+            if (a.weights) a.weights[pix * L + k] = Wt[s];
+        }
+    }
+    const int C = a.C;
+    for (int c = 0; c < C; ++c) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int s = 0; s < KM; ++s)
+            if (s >= KM - K && key[s] < INFINITY) acc = fmaf(Wt[s], __ldg(a.attr + (int64_t)id[s] * C + c), acc);
+        a.image[pix * C + c] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generic path for list lengths above the register lists (L > 32): same tile
+// staging, the per-pixel list kept sorted in the workspace.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_render_generic(Args a) {
+    constexpr int NT = 256, TH = 16;
+    extern __shared__ float4 smem[];
+    float4* stage = smem;
+    int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
+    float* skey = reinterpret_cast<float*>(sgid + NT);
+    int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
+
+    const CamDev* cams = a.ws.cams;
+    const int t = blockIdx.x;
+    const int v = find_view(cams, a.B, t);
+    const int lt = t - __ldg(&cams[v].tile_base);
+    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int tx = lt % tiles_x, ty = lt / tiles_x;
+    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
+    const int tid = threadIdx.x;
+    const int j = tx * kTileW + (tid & 15);
+    const int i = ty * TH + (tid >> 4);
+    const bool valid = (i < H) && (j < W);
+    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
+    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
+    const int64_t vb = (int64_t)v * a.N;
+    const int L = a.L;
+    float* lk = a.ws.gkey + pix * L;
+    int32_t* li = a.ws.gid + pix * L;
+    int n = 0;
+
+    const TileSrc src = tile_source<NT>(a, t, tx, ty, v, skey, sid);
+    bool active = valid;
+    for (int base = 0; base < src.count; base += NT) {
+        const int nc = min(NT, src.count - base);
+        if (tid < nc) {
+            int32_t g;
+            if (src.mode == 1) g = sid[base + tid];
+            else if (src.mode == 0) g = a.ws.tile_gauss[src.start + base + tid];
+            else g = base + tid;
+            float4 r0, r1, r2, r3;
+            load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+            if (src.filter_box) {
+                const int4 tb = a.ws.tbox[vb + g];
+                if (tx < tb.x || tx > tb.y || ty < tb.z || ty > tb.w) {
+                    r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    r2 = r1;
+                }
+            }
+            stage[tid] = r0;
+            stage[NT + tid] = r1;
+            stage[2 * NT + tid] = r2;
+            stage[3 * NT + tid] = r3;
+            sgid[tid] = g;
+        }
+        __syncthreads();
+        if (active) {
+            for (int q = 0; q < nc; ++q) {
+                const float4 r3 = stage[3 * NT + q];
+                const float kth = (n == L) ? lk[L - 1] : INFINITY;
+                if (src.mode == 1 && r3.w > kth) {
+                    active = false;
+                    break;
+                }
+                const float l = candidate_key(stage[q], stage[NT + q], stage[2 * NT + q], r3, px, py, a.Qeta);
+                if (l > 0.0f) {
+                    const int32_t g = sgid[q];
+                    if (n < L || l < lk[L - 1] || (l == lk[L - 1] && g < li[L - 1])) {
+                        int p = (n < L) ? n : L - 1;
+                        while (p > 0 && (lk[p - 1] > l || (lk[p - 1] == l && li[p - 1] > g))) {
+                            lk[p] = lk[p - 1];
+                            li[p] = li[p - 1];
+                            --p;
+                        }
+                        lk[p] = l;
+                        li[p] = g;
+                        if (n < L) ++n;
+                    }
+                }
+            }
+        }
+        if (__syncthreads_and(!active)) break;
+    }
+    if (!valid) return;
+    // fine pass with both loops over the list in global memory (L1 resident)
+    float* lw = a.weights ? a.weights + pix * L : nullptr;
+    for (int k = 0; k < n; ++k) {
+        float4 r0, r1, r2, r3;
+        load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
+        const Entry ek = entry_px(r0, r1, r2, r3, px, py);
+        float A = 0.0f;
+        for (int jj = 0; jj < n; ++jj) {
+            load_rec(a.ws.rec, vb + li[jj], r0, r1, r2, r3);
+            const Entry ej = entry_px(r0, r1, r2, r3, px, py);
+            const float u = ((ek.hi - ej.hi) + (ek.lo - ej.lo)) * ej.r;
+            const float q = erfc_as28(fabsf(u));
+            const float m = 0.5f * ej.a;
+            const float sm = copysignf(m, u);
+            A = fmaf(-sm, q, A + (m + sm));
+        }
+        lk[k] = ex2_approx(-a.tau * kLog2e * A) * ek.a;  // reuse the key slot for W_k
+    }
+    for (int k = 0; k < L; ++k) {
+        const bool real = k < n;
+        a.index[pix * L + k] = real ? li[k] : -1;
+        if (lw) lw[k] = real ? lk[k] : 0.0f;
+    }
+    for (int c = 0; c < a.C; ++c) {
+        float acc = 0.0f;
+        for (int k = 0; k < n; ++k) acc = fmaf(lk[k], __ldg(a.attr + (int64_t)li[k] * a.C + c), acc);
+        a.image[pix * a.C + c] = acc;
+    }
+}
+
+size_t render_smem_bytes(int KM, int TH) {
+    const int NT = 16 * TH;
+    const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)kSortMax * 8;
+    const size_t phase2 = (size_t)KM * NT * 16;
+    return phase1 > phase2 ? phase1 : phase2;
+}
+
+template <typename Kern>
+static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthreads, size_t smem, cudaStream_t s,
+                                const Args& a) {
+    TraceScope tr(name, s);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<nblocks, nthreads, smem, s>>>(a);
+    return cudaPeekAtLastError();
+}
+
+// Launch the forward tile kernel for register-list capacity KM (0 = generic).
+cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a) {
+    switch (KM) {
+        case 8: return launch_tiles(k_render<8, 16>, "k_render<8>", nblocks, 256, render_smem_bytes(8, 16), s, a);
+        case 16: return launch_tiles(k_render<16, 16>, "k_render<16>", nblocks, 256, render_smem_bytes(16, 16), s, a);
+        case 20: return launch_tiles(k_render<20, 16>, "k_render<20>", nblocks, 256, render_smem_bytes(20, 16), s, a);
+        case 24: return launch_tiles(k_render<24, 16>, "k_render<24>", nblocks, 256, render_smem_bytes(24, 16), s, a);
+        case 32: return launch_tiles(k_render<32, 8>, "k_render<32>", nblocks, 128, render_smem_bytes(32, 8), s, a);
+        default: return launch_tiles(k_render_generic, "k_render_generic", nblocks, 256, render_smem_bytes(0, 16), s, a);
+    }
+}
+
+}  // namespace voge

@@ -1,0 +1,233 @@
+// voge_project.cu -- viewing transform, per-(view, Gaussian) records and
+// tile binning (the coarse stage's culling).
+//
+// Sec. 3.3 (viewing transformation): M = R M_w + T, P = R P_w Rᵀ.
+// App. A.3 (coarse rasterisation role): the paper rasterises a per-ellipsoid
+// screen box at 1/8 resolution into a pixel->kernel assignment.  Here the box
+// is the exact bounding box of the conic {pixels : e^{q} > eta} (plus a
+// safety margin), binned into 16 x TH pixel tiles with a count / scan /
+// scatter, so that a pixel only traces the Gaussians of its tile and the
+// culling never changes a result.
+#include "voge_device.cuh"
+#include "voge_trace.cuh"
+
+namespace voge {
+
+__global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams, Args a, int count_tiles) {
+    const int64_t BN = (int64_t)a.B * a.N;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    const int v = (int)(t / a.N);
+    const int g = (int)(t - (int64_t)v * a.N);
+    const CamDev& c = cams[v];
+    float R[9], T[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) R[q] = __ldg(&c.R[q]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) T[q] = __ldg(&c.T[q]);
+    const float F = __ldg(&c.F), Ox = __ldg(&c.Ox), Oy = __ldg(&c.Oy), invF = __ldg(&c.invF);
+    const int H = __ldg(&c.H), W = __ldg(&c.W), tiles_x = __ldg(&c.tiles_x), tile_h = __ldg(&c.tile_h);
+    const int tile_base = __ldg(&c.tile_base);
+
+    const float X = __ldg(a.means + 3 * (int64_t)g), Y = __ldg(a.means + 3 * (int64_t)g + 1),
+                Z = __ldg(a.means + 3 * (int64_t)g + 2);
+    float pw[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) pw[q] = __ldg(a.inv_cov + 6 * (int64_t)g + q);
+
+    // camera-space mean in double-float
+    dfl Mx = df_dot3_add(R[0], X, R[1], Y, R[2], Z, T[0]);
+    dfl My = df_dot3_add(R[3], X, R[4], Y, R[5], Z, T[1]);
+    dfl Mz = df_dot3_add(R[6], X, R[7], Y, R[8], Z, T[2]);
+
+    // camera-space inverse covariance P = R Pw Rᵀ
+    const float Pw[9] = {pw[0], pw[1], pw[2], pw[1], pw[3], pw[4], pw[2], pw[4], pw[5]};
+    float A[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[3 * i + j] = fmaf(R[3 * i], Pw[j], fmaf(R[3 * i + 1], Pw[3 + j], R[3 * i + 2] * Pw[6 + j]));
+    float P[6];  // xx xy xz yy yz zz
+    P[0] = fmaf(A[0], R[0], fmaf(A[1], R[1], A[2] * R[2]));
+    P[1] = fmaf(A[0], R[3], fmaf(A[1], R[4], A[2] * R[5]));
+    P[2] = fmaf(A[0], R[6], fmaf(A[1], R[7], A[2] * R[8]));
+    P[3] = fmaf(A[3], R[3], fmaf(A[4], R[4], A[5] * R[5]));
+    P[4] = fmaf(A[3], R[6], fmaf(A[4], R[7], A[5] * R[8]));
+    P[5] = fmaf(A[6], R[6], fmaf(A[7], R[7], A[8] * R[8]));
+
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+    float4 s0 = make_float4(P[0], P[1], P[2], P[3]);
+    float4 s1 = make_float4(P[4], P[5], 0.f, 0.f);
+    int4 tb = make_int4(1, 0, 1, 0);  // empty
+
+    bool valid = Mz.hi > 0.0f && isfinite(Mz.hi) && isfinite(Mx.hi) && isfinite(My.hi);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) valid = valid && isfinite(P[q]);
+    if (valid) {
+        const dfl xh = df_div(Mx, Mz), yh = df_div(My, Mz);
+        const dfl uc = df_add(df_mul_f(xh, F), dfl{Ox, 0.0f});
+        const dfl vc = df_add(df_mul_f(yh, F), dfl{Oy, 0.0f});
+        const float x = xh.hi, y = yh.hi;
+        // g = P Mh, beta0 = Mhᵀ P Mh
+        const float gx = fmaf(P[0], x, fmaf(P[1], y, P[2]));
+        const float gy = fmaf(P[1], x, fmaf(P[3], y, P[4]));
+        const float gz = fmaf(P[2], x, fmaf(P[4], y, P[5]));
+        const float beta0 = fmaf(gx, x, fmaf(gy, y, gz));
+        const float invF2 = invF * invF;
+        // adjugate of P (symmetric)
+        const float a00 = fmaf(P[3], P[5], -P[4] * P[4]);
+        const float a01 = fmaf(P[2], P[4], -P[1] * P[5]);
+        const float a02 = fmaf(P[1], P[4], -P[2] * P[3]);
+        const float a11 = fmaf(P[0], P[5], -P[2] * P[2]);
+        const float a12 = fmaf(P[1], P[2], -P[0] * P[4]);
+        const float a22 = fmaf(P[0], P[3], -P[1] * P[1]);
+        // (M x D') = Mz (du c1 + dv c2)/F with c1 = (0, 1, -y), c2 = (-1, 0, x)
+        const float c11 = fmaf(y, fmaf(a22, y, -2.0f * a12), a11);
+        const float c22 = fmaf(x, fmaf(a22, x, -2.0f * a02), a00);
+        const float c12 = fmaf(a12, x, fmaf(a02, y, fmaf(-a22 * x, y, -a01)));
+        const float mzf = Mz.hi * invF;
+        const float s2 = mzf * mzf;
+        r0 = make_float4(uc.hi, uc.lo, vc.hi, vc.lo);
+        r1 = make_float4(beta0, gx * invF, gy * invF, P[0] * invF2);
+        r2 = make_float4(2.0f * P[1] * invF2, P[3] * invF2, s2 * c11, 2.0f * s2 * c12);
+        // depth bound: l D is inside the ellipsoid (X-M)ᵀP(X-M) <= Qeta, so
+        // |l - Mz| <= sqrt(Qeta Sigma_zz), Sigma_zz = a22 / det P.
+        const float detP = fmaf(P[0], a00, fmaf(P[1], a01, P[2] * a02));
+        float lmin = -INFINITY;
+        if (a.use_thresh && detP > 0.0f && a22 > 0.0f) {
+            const float h = sqrtf(a.Qeta * a22 / detP);
+            lmin = Mz.hi - (1.001f * h + 1e-6f * Mz.hi);
+        }
+        r3 = make_float4(s2 * c22, Mz.hi, Mz.lo, lmin);
+        s1.z = x;
+        s1.w = y;
+
+        // tile box of the conic qb - Qeta b < 0 (pixel units)
+        int j0 = 0, j1 = W - 1, i0 = 0, i1 = H - 1;
+        bool empty = false;
+        if (a.use_thresh) {
+            const float Q = a.Qeta;
+            const float h00 = fmaf(-Q, r1.w, r2.z);
+            const float h01 = fmaf(-Q, 0.5f * r2.x, 0.5f * r2.w);
+            const float h11 = fmaf(-Q, r2.y, r3.x);
+            const float hx = -Q * r1.y, hy = -Q * r1.z, h22 = -Q * beta0;
+            const float det = fmaf(h00, h11, -h01 * h01);
+            if (h00 > 0.0f && det > 1e-12f * h00 * h11 && isfinite(det)) {
+                const float id = 1.0f / det;
+                const float cx = -(h11 * hx - h01 * hy) * id;
+                const float cy = -(h00 * hy - h01 * hx) * id;
+                const float f0 = h22 + hx * cx + hy * cy;
+                if (!(f0 < 0.0f)) {
+                    empty = true;
+                } else {
+                    const float xr = sqrtf(-f0 * h11 * id) * 1.02f + 1.0f;
+                    const float yr = sqrtf(-f0 * h00 * id) * 1.02f + 1.0f;
+                    const float ucx = uc.hi + cx - 0.5f, vcy = vc.hi + cy - 0.5f;
+                    const float fj0 = floorf(ucx - xr), fj1 = ceilf(ucx + xr);
+                    const float fi0 = floorf(vcy - yr), fi1 = ceilf(vcy + yr);
+                    if (isfinite(fj0) && isfinite(fj1) && isfinite(fi0) && isfinite(fi1)) {
+                        if (fj1 < 0.0f || fi1 < 0.0f || fj0 > (float)(W - 1) || fi0 > (float)(H - 1)) {
+                            empty = true;
+                        } else {
+                            j0 = max(0, (int)fmaxf(fj0, -1.0f));
+                            j1 = min(W - 1, (int)fminf(fj1, (float)W));
+                            i0 = max(0, (int)fmaxf(fi0, -1.0f));
+                            i1 = min(H - 1, (int)fminf(fi1, (float)H));
+                        }
+                    }
+                }
+            }
+        }
+        if (!empty && W > 0 && H > 0) tb = make_int4(j0 / kTileW, j1 / kTileW, i0 / tile_h, i1 / tile_h);
+    }
+    a.ws.rec[4 * t + 0] = r0;
+    a.ws.rec[4 * t + 1] = r1;
+    a.ws.rec[4 * t + 2] = r2;
+    a.ws.rec[4 * t + 3] = r3;
+    a.ws.rec2[2 * t + 0] = s0;
+    a.ws.rec2[2 * t + 1] = s1;
+    a.ws.tbox[t] = tb;
+    if (count_tiles) {
+        for (int ty = tb.z; ty <= tb.w; ++ty)
+            for (int tx = tb.x; tx <= tb.y; ++tx) atomicAdd(&a.ws.tile_cnt[tile_base + ty * tiles_x + tx], 1);
+    }
+}
+
+// Exclusive scan of the per-tile counts (one CTA of 1024 threads; each thread
+// owns a contiguous run).  Also seeds the scatter cursors.
+__global__ void __launch_bounds__(1024) k_scan_tiles(Ws ws) {
+    __shared__ int32_t warp_sums[32];
+    const int n = ws.total_tiles;
+    const int tid = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int beg = min(n, tid * per), end = min(n, beg + per);
+    int32_t s = 0;
+    for (int q = beg; q < end; ++q) s += ws.tile_cnt[q];
+    // block exclusive scan of s
+    int32_t x = s;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int32_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0);
+    for (int q = beg; q < end; ++q) {
+        ws.tile_off[q] = run;
+        ws.tile_cur[q] = run;
+        run += ws.tile_cnt[q];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const CamDev* __restrict__ cams, Args a) {
+    const int64_t BN = (int64_t)a.B * a.N;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    const int4 tb = a.ws.tbox[t];
+    if (tb.x > tb.y) return;
+    const int v = (int)(t / a.N);
+    const int g = (int)(t - (int64_t)v * a.N);
+    const int tiles_x = __ldg(&cams[v].tiles_x), tile_base = __ldg(&cams[v].tile_base);
+    for (int ty = tb.z; ty <= tb.w; ++ty)
+        for (int tx = tb.x; tx <= tb.y; ++tx) {
+            int pos = atomicAdd(&a.ws.tile_cur[tile_base + ty * tiles_x + tx], 1);
+            if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
+        }
+}
+
+// Upload-free part of the projection: k_project, then (with count_tiles) the
+// tile scan and scatter.
+cudaError_t launch_project(int64_t BN, int count_tiles, cudaStream_t s, const Args& a) {
+    if (BN > 0) {
+        TraceScope tr("k_project", s);
+        k_project<<<(unsigned)((BN + 255) / 256), 256, 0, s>>>(a.ws.cams, a, count_tiles);
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (count_tiles) {
+        {
+            TraceScope tr("k_scan_tiles", s);
+            k_scan_tiles<<<1, 1024, 0, s>>>(a.ws);
+        }
+        if (BN > 0) {
+            TraceScope tr("k_scatter", s);
+            k_scatter<<<(unsigned)((BN + 255) / 256), 256, 0, s>>>(a.ws.cams, a);
+        }
+        return cudaPeekAtLastError();
+    }
+    return cudaSuccess;
+}
+
+}  // namespace voge

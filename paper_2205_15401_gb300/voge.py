@@ -1,0 +1,295 @@
+"""Python binding of libvoge.so: argument marshalling only.
+
+Every function named ``voge_*`` mirrors the C entry point of the same name in
+``include/voge.h``: it converts torch tensors to device pointers, the current
+torch stream to a ``cudaStream_t`` and camera dicts to ``voge_camera``
+structs, and calls the library.  There is no fallback: if ``libvoge.so`` has
+not been built, or a call fails, a RuntimeError is raised.
+
+On top of the binding sit ``Renderer`` (workspace management) and
+``VoGERender`` (a ``torch.autograd.Function`` whose forward is
+``voge_render_fwd`` and whose backward is ``voge_render_bwd``; it saves only
+the per-pixel index lists).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvoge.so")
+_lock = threading.Lock()
+_lib = None
+
+VOGE_OK = 0
+VOGE_FLAG_PLAIN = 1
+VOGE_FLAG_REUSE_PROJECTION = 2
+
+
+class voge_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("T", ctypes.c_float * 3), ("F", ctypes.c_float),
+                ("Ox", ctypes.c_float), ("Oy", ctypes.c_float), ("H", ctypes.c_int32), ("W", ctypes.c_int32)]
+
+
+class voge_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class voge_params(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("tau", ctypes.c_float), ("thresh", ctypes.c_float), ("flags", ctypes.c_int32),
+                ("bin_capacity", ctypes.c_int32)]
+
+
+def lib():
+    """Load libvoge.so (built in-tree); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_15401_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, P = ctypes.c_void_p, ctypes.POINTER
+            L.voge_version.restype = ctypes.c_int
+            L.voge_strerror.restype = ctypes.c_char_p
+            L.voge_strerror.argtypes = [ctypes.c_int]
+            L.voge_list_length.argtypes = [P(voge_params)]
+            L.voge_list_length.restype = ctypes.c_int
+            L.voge_workspace_bytes.argtypes = [P(voge_camera), P(voge_params)]
+            L.voge_workspace_bytes.restype = ctypes.c_size_t
+            L.voge_render_fwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+            L.voge_render_fwd.restype = ctypes.c_int
+            L.voge_render_bwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                          ctypes.c_size_t, vp]
+            L.voge_render_bwd.restype = ctypes.c_int
+            L.voge_pose_to_RT.argtypes = [P(ctypes.c_double), P(ctypes.c_float), P(ctypes.c_float)]
+            L.voge_pose_to_RT.restype = None
+            L.voge_pose_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+            L.voge_pose_grad.restype = ctypes.c_int
+            L.voge_mse_grad.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+            L.voge_mse_grad.restype = ctypes.c_int
+            L.voge_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_int32, vp]
+            L.voge_adam_step.restype = ctypes.c_int
+            L.voge_trace_enable.argtypes = [ctypes.c_int]
+            L.voge_trace_enable.restype = ctypes.c_int
+            L.voge_trace_read.argtypes = [P(voge_trace_entry), ctypes.c_int]
+            L.voge_trace_read.restype = ctypes.c_int
+            L.voge_trace_reset.restype = None
+            _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != VOGE_OK:
+        raise RuntimeError(f"{what} failed: {lib().voge_strerror(rc).decode()} ({rc})")
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_cameras(cams):
+    """List of dicts (R 3x3, T 3, F, Ox, Oy, H, W) -> ctypes array of voge_camera."""
+    arr = (voge_camera * len(cams))()
+    for v, c in enumerate(cams):
+        R = np.asarray(c["R"], dtype=np.float32).reshape(9)
+        T = np.asarray(c["T"], dtype=np.float32).reshape(3)
+        for q in range(9):
+            arr[v].R[q] = float(R[q])
+        for q in range(3):
+            arr[v].T[q] = float(T[q])
+        arr[v].F, arr[v].Ox, arr[v].Oy = float(c["F"]), float(c["Ox"]), float(c["Oy"])
+        arr[v].H, arr[v].W = int(c["H"]), int(c["W"])
+    return arr
+
+
+def make_params(B, N, C, K, tau, thresh, flags=0, bin_capacity=0):
+    return voge_params(int(B), int(N), int(C), int(K), float(tau), float(thresh), int(flags), int(bin_capacity))
+
+
+# ----------------------------------------------------------------- C ABI ---
+def voge_version():
+    return int(lib().voge_version())
+
+
+def voge_list_length(params):
+    return int(lib().voge_list_length(ctypes.byref(params)))
+
+
+def voge_workspace_bytes(cams, params):
+    n = lib().voge_workspace_bytes(cams, ctypes.byref(params))
+    if n == 0:
+        raise RuntimeError("voge_workspace_bytes: invalid cameras or parameters")
+    return int(n)
+
+
+def voge_render_fwd(cams, params, means, inv_cov, attr, image, weights, index, workspace, stream=None):
+    f32, i32 = torch.float32, torch.int32
+    rc = lib().voge_render_fwd(cams, ctypes.byref(params), _ptr(means, f32), _ptr(inv_cov, f32), _ptr(attr, f32),
+                               _ptr(image, f32), _ptr(weights, f32), _ptr(index, i32), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "voge_render_fwd")
+
+
+def voge_render_bwd(cams, params, means, inv_cov, attr, index, grad_image, grad_means, grad_inv_cov, grad_attr,
+                    grad_cam, workspace, stream=None):
+    f32, i32 = torch.float32, torch.int32
+    rc = lib().voge_render_bwd(cams, ctypes.byref(params), _ptr(means, f32), _ptr(inv_cov, f32), _ptr(attr, f32),
+                               _ptr(index, i32), _ptr(grad_image, f32), _ptr(grad_means, f32),
+                               _ptr(grad_inv_cov, f32), _ptr(grad_attr, f32), _ptr(grad_cam, f32),
+                               _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "voge_render_bwd")
+
+
+def voge_pose_to_RT(pose):
+    p = (ctypes.c_double * 4)(*[float(x) for x in np.asarray(pose, dtype=np.float64).reshape(4)])
+    R = (ctypes.c_float * 9)()
+    T = (ctypes.c_float * 3)()
+    lib().voge_pose_to_RT(p, R, T)
+    return np.array(R[:], np.float32).reshape(3, 3), np.array(T[:], np.float32)
+
+
+def voge_pose_grad(pose, grad_cam, grad_pose, stream=None):
+    B = pose.shape[0]
+    f32 = torch.float32
+    _check(lib().voge_pose_grad(_ptr(pose, f32), _ptr(grad_cam, f32), _ptr(grad_pose, f32), B, _stream(stream)),
+           "voge_pose_grad")
+
+
+def voge_mse_grad(image, target, grad_image, loss, stream=None):
+    f32 = torch.float32
+    _check(lib().voge_mse_grad(_ptr(image, f32), _ptr(target, f32), image.numel(), _ptr(grad_image, f32),
+                               _ptr(loss, f32), _stream(stream)), "voge_mse_grad")
+
+
+def voge_adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    f32 = torch.float32
+    _check(lib().voge_adam_step(_ptr(param, f32), _ptr(grad, f32), _ptr(m, f32), _ptr(v, f32), param.numel(),
+                                float(lr), float(beta1), float(beta2), float(eps), int(step), _stream(stream)),
+           "voge_adam_step")
+
+
+def voge_trace_enable(on=True):
+    return bool(lib().voge_trace_enable(1 if on else 0))
+
+
+def voge_trace_read():
+    """{kernel name: (launches, total device ms)} accumulated since the last reset."""
+    buf = (voge_trace_entry * 64)()
+    n = lib().voge_trace_read(buf, 64)
+    return {buf[q].name.decode(): (int(buf[q].launches), float(buf[q].total_ms)) for q in range(min(n, 64))}
+
+
+def voge_trace_reset():
+    lib().voge_trace_reset()
+
+
+# -------------------------------------------------------------- helpers ---
+def cameras_from_poses(poses, F, H, W):
+    """Camera dicts for poses (azim, elev, dist, roll) through voge_pose_to_RT."""
+    out = []
+    for p in np.asarray(poses, dtype=np.float64).reshape(-1, 4):
+        R, T = voge_pose_to_RT(p)
+        out.append({"R": R, "T": T, "F": float(F), "Ox": W / 2.0, "Oy": H / 2.0, "H": int(H), "W": int(W)})
+    return out
+
+
+class Renderer:
+    """Cameras + parameters + a cached device workspace for repeated renders."""
+
+    def __init__(self, cams, N, C, K=20, tau=1.0, thresh=0.01, flags=0, bin_capacity=0, device="cuda"):
+        self.cam_list = list(cams)
+        self.cams = make_cameras(self.cam_list)
+        self.params = make_params(len(self.cam_list), N, C, K, tau, thresh, flags, bin_capacity)
+        self.L = voge_list_length(self.params)
+        self.pixels = sum(int(c["H"]) * int(c["W"]) for c in self.cam_list)
+        self.device = torch.device(device)
+        nbytes = voge_workspace_bytes(self.cams, self.params)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def set_cameras(self, cams):
+        self.cam_list = list(cams)
+        assert len(self.cam_list) == self.params.B
+        self.cams = make_cameras(self.cam_list)
+        nbytes = voge_workspace_bytes(self.cams, self.params)
+        if nbytes > self.workspace.numel():
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def alloc_outputs(self):
+        P, C, L = self.pixels, self.params.C, self.L
+        image = torch.empty((P, C), dtype=torch.float32, device=self.device)
+        weights = torch.empty((P, max(L, 1)), dtype=torch.float32, device=self.device)
+        index = torch.empty((P, max(L, 1)), dtype=torch.int32, device=self.device)
+        return image, weights, index
+
+    def forward(self, means, inv_cov, attr, out=None, flags=None):
+        image, weights, index = out if out is not None else self.alloc_outputs()
+        params = self.params if flags is None else make_params(self.params.B, self.params.N, self.params.C,
+                                                               self.params.K, self.params.tau, self.params.thresh,
+                                                               flags, self.params.bin_capacity)
+        voge_render_fwd(self.cams, params, means, inv_cov, attr, image, weights, index, self.workspace)
+        return image, weights, index
+
+    def backward(self, means, inv_cov, attr, index, grad_image, grad_means=None, grad_inv_cov=None, grad_attr=None,
+                 grad_cam=None, reuse_projection=False):
+        params = self.params
+        if reuse_projection:
+            params = make_params(params.B, params.N, params.C, params.K, params.tau, params.thresh,
+                                 params.flags | VOGE_FLAG_REUSE_PROJECTION, params.bin_capacity)
+        voge_render_bwd(self.cams, params, means, inv_cov, attr, index, grad_image, grad_means, grad_inv_cov,
+                        grad_attr, grad_cam, self.workspace)
+
+
+class VoGERender(torch.autograd.Function):
+    """image = VoGERender.apply(means, inv_cov, attr, renderer, cam_grad_holder).
+
+    Gradients flow to means [N,3], inv_cov [N,6] and attr [N,C].  If
+    ``cam_grad_holder`` is a tensor of shape [B,12], dL/d(R,T) of each view is
+    accumulated into it during backward (for pose fitting)."""
+
+    @staticmethod
+    def forward(ctx, means, inv_cov, attr, renderer, cam_grad=None):
+        means, inv_cov, attr = means.contiguous(), inv_cov.contiguous(), attr.contiguous()
+        image, weights, index = renderer.forward(means, inv_cov, attr)
+        ctx.renderer = renderer
+        ctx.cam_grad = cam_grad
+        ctx.save_for_backward(means, inv_cov, attr, index)
+        ctx.mark_non_differentiable(weights, index)
+        return image, weights, index
+
+    @staticmethod
+    def backward(ctx, grad_image, grad_w=None, grad_i=None):
+        means, inv_cov, attr, index = ctx.saved_tensors
+        r = ctx.renderer
+        gm = torch.zeros_like(means) if ctx.needs_input_grad[0] else None
+        gp = torch.zeros_like(inv_cov) if ctx.needs_input_grad[1] else None
+        ga = torch.zeros_like(attr) if ctx.needs_input_grad[2] else None
+        if grad_image is None:
+            return gm, gp, ga, None, None
+        r.backward(means, inv_cov, attr, index, grad_image.contiguous(), gm, gp, ga, ctx.cam_grad)
+        return gm, gp, ga, None, None
+
+
+def render(means, inv_cov, attr, renderer, cam_grad=None):
+    """Differentiable render; returns (image [P,C], weights [P,L], index [P,L])."""
+    return VoGERender.apply(means, inv_cov, attr, renderer, cam_grad)
