@@ -21,8 +21,10 @@ namespace voge {
 
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
+// Camera-space gradient of one (pixel, kept Gaussian) pair: out[0..2] = dM,
+// out[3..8] = G (xx, xy, xz, yy, yz, zz) with entries of P treated as independent.
 __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, float px, float py, float invF, float dqt,
-                                                float dl, float db) {
+                                                float dl, float db, float out[9]) {
     float4 r0, r1, r2, r3;
     load_rec(a.ws.rec, o, r0, r1, r2, r3);
     const float4 s0 = __ldg(a.ws.rec2 + 2 * o), s1 = __ldg(a.ws.rec2 + 2 * o + 1);
@@ -42,16 +44,15 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, float 
     const float PD1 = fmaf(Pxy, D0, fmaf(Pyy, D1, Pyz));
     const float PD2 = fmaf(Pxz, D0, fmaf(Pyz, D1, Pzz));
     const float q2 = 2.0f * dqt, lb = dl * ib, lh = 0.5f * lb;
-    float* gc = a.ws.gcam + 9 * o;
-    atomicAdd(gc + 0, fmaf(q2, PV0, lb * PD0));
-    atomicAdd(gc + 1, fmaf(q2, PV1, lb * PD1));
-    atomicAdd(gc + 2, fmaf(q2, PV2, lb * PD2));
-    atomicAdd(gc + 3, fmaf(dqt, V0 * V0, fmaf(lb, V0 * D0, db * D0 * D0)));
-    atomicAdd(gc + 4, fmaf(dqt, V0 * V1, fmaf(lh, fmaf(V0, D1, D0 * V1), db * D0 * D1)));
-    atomicAdd(gc + 5, fmaf(dqt, V0 * V2, fmaf(lh, fmaf(V0, 1.0f, D0 * V2), db * D0)));
-    atomicAdd(gc + 6, fmaf(dqt, V1 * V1, fmaf(lb, V1 * D1, db * D1 * D1)));
-    atomicAdd(gc + 7, fmaf(dqt, V1 * V2, fmaf(lh, fmaf(V1, 1.0f, D1 * V2), db * D1)));
-    atomicAdd(gc + 8, fmaf(dqt, V2 * V2, fmaf(lb, V2, db)));
+    out[0] = fmaf(q2, PV0, lb * PD0);
+    out[1] = fmaf(q2, PV1, lb * PD1);
+    out[2] = fmaf(q2, PV2, lb * PD2);
+    out[3] = fmaf(dqt, V0 * V0, fmaf(lb, V0 * D0, db * D0 * D0));
+    out[4] = fmaf(dqt, V0 * V1, fmaf(lh, fmaf(V0, D1, D0 * V1), db * D0 * D1));
+    out[5] = fmaf(dqt, V0 * V2, fmaf(lh, fmaf(V0, 1.0f, D0 * V2), db * D0));
+    out[6] = fmaf(dqt, V1 * V1, fmaf(lb, V1 * D1, db * D1 * D1));
+    out[7] = fmaf(dqt, V1 * V2, fmaf(lh, fmaf(V1, 1.0f, D1 * V2), db * D1));
+    out[8] = fmaf(dqt, V2 * V2, fmaf(lb, V2, db));
 }
 
 template <int KM, int TH>
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
     const int tid = threadIdx.x;
     const int j = tx * kTileW + (tid & 15);
     const int i = ty * TH + (tid >> 4);
-    if (i >= H || j >= W) return;  // no block-wide barriers below
+    const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
     const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
     const int64_t vb = (int64_t)v * a.N;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
 
     int32_t id[KM];
     float hi[KM], lo[KM], dA[KM], dl[KM];
+    if (!valid) return;  // no block-wide barriers in this kernel
     int n = 0;
     bool open = true;
 #pragma unroll
@@ -104,7 +106,6 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
             }
         }
     }
-    if (n == 0) return;
     // loop 1: A_k
     float A[KM];
 #pragma unroll
@@ -175,7 +176,11 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
                 const Entry en = entry_px(r0, r1, r2, r3, px, py);
                 const float dqt = fmaf(dA[s], inv2tau, -0.25f * en.a * J.x);
                 const float db = J.z / (4.0f * en.r);
-                chain_to_camera(a, o, px, py, invF, dqt, dl[s] + J.y, db);
+                float gv[9];
+                chain_to_camera(a, o, px, py, invF, dqt, dl[s] + J.y, db, gv);
+                float* gc = a.ws.gcam + 9 * o;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) atomicAdd(gc + q, gv[q]);
                 ++e;
             }
         }
@@ -258,7 +263,10 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a) {
         const float* sk = S + 8 * k;
         const float dqt = fmaf(sk[4], inv2tau, -0.5f * sk[3] * sk[6]);  // a/4 = m/2
         const float db = sk[7] / (4.0f * sk[2]);
-        chain_to_camera(a, vb + li[k], px, py, invF, dqt, sk[5], db);
+        float gv[9];
+        chain_to_camera(a, vb + li[k], px, py, invF, dqt, sk[5], db, gv);
+        float* gc = a.ws.gcam + 9 * (vb + li[k]);
+        for (int q = 0; q < 9; ++q) atomicAdd(gc + q, gv[q]);
     }
 }
 
@@ -349,14 +357,19 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
     return cudaPeekAtLastError();
 }
 
+template <int KM, int TH>
+static size_t backward_smem_bytes() {
+    return (size_t)KM * 16 * TH * 16;
+}
+
 // Launch the backward tile kernel for register-list capacity KM (0 = generic).
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a) {
     switch (KM) {
-        case 8: return launch_tiles(k_backward<8, 16>, "k_backward<8>", nblocks, 256, (size_t)8 * 256 * 16, s, a);
-        case 16: return launch_tiles(k_backward<16, 16>, "k_backward<16>", nblocks, 256, (size_t)16 * 256 * 16, s, a);
-        case 20: return launch_tiles(k_backward<20, 16>, "k_backward<20>", nblocks, 256, (size_t)20 * 256 * 16, s, a);
-        case 24: return launch_tiles(k_backward<24, 16>, "k_backward<24>", nblocks, 256, (size_t)24 * 256 * 16, s, a);
-        case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, (size_t)32 * 128 * 16, s, a);
+        case 8: return launch_tiles(k_backward<8, 16>, "k_backward<8>", nblocks, 256, backward_smem_bytes<8, 16>(), s, a);
+        case 16: return launch_tiles(k_backward<16, 16>, "k_backward<16>", nblocks, 256, backward_smem_bytes<16, 16>(), s, a);
+        case 20: return launch_tiles(k_backward<20, 16>, "k_backward<20>", nblocks, 256, backward_smem_bytes<20, 16>(), s, a);
+        case 24: return launch_tiles(k_backward<24, 16>, "k_backward<24>", nblocks, 256, backward_smem_bytes<24, 16>(), s, a);
+        case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, backward_smem_bytes<32, 8>(), s, a);
         default: return launch_tiles(k_backward_generic, "k_backward_generic", nblocks, 256, 0, s, a);
     }
 }

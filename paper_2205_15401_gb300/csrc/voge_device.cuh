@@ -206,18 +206,67 @@ __device__ __forceinline__ void load_rec(const float4* __restrict__ rec, int64_t
 }
 
 // Sorted insertion into a register list of KM (key, id) pairs, ascending by
-// (key, id).  The caller has checked that (l, g) beats the last entry.
+// (key, id).  The caller has checked that (l, g) beats the last entry.  All
+// comparisons are made against the old list first (the flags are monotone in
+// s because the list is sorted), then every slot is updated independently, so
+// the insertion has no serial dependency chain through the list.
 template <int KM>
 __device__ __forceinline__ void topk_insert(float (&key)[KM], int32_t (&id)[KM], float l, int32_t g) {
+    bool lt[KM];
 #pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        bool lt = (l < key[s]) || (l == key[s] && g < id[s]);
-        float tk = lt ? key[s] : l;
-        int32_t ti = lt ? id[s] : g;
-        key[s] = lt ? l : key[s];
-        id[s] = lt ? g : id[s];
-        l = tk;
-        g = ti;
+    for (int s = 0; s < KM; ++s) lt[s] = (l < key[s]) || (l == key[s] && g < id[s]);
+#pragma unroll
+    for (int s = KM - 1; s >= 1; --s) {
+        key[s] = lt[s] ? (lt[s - 1] ? key[s - 1] : l) : key[s];
+        id[s] = lt[s] ? (lt[s - 1] ? id[s - 1] : g) : id[s];
+    }
+    key[0] = lt[0] ? l : key[0];
+    id[0] = lt[0] ? g : id[0];
+}
+
+// Column interval of each tile row in which the candidate test can pass.
+// Per row the test qb < Qeta b is the quadratic inequality
+//   h00 du^2 + 2 (h01 dv + hx) du + (h11 dv^2 + 2 hy dv + h22) < 0,
+// an interval of du whenever h00 > 0.  The interval is widened by 1 pixel
+// plus 2% of its half-width, so it never excludes a pixel that the exact
+// per-pixel test keeps; rows with h00 <= 0 (or no threshold) are left whole.
+// Output: tile-local columns packed as lo | hi << 8 (lo > hi: empty row).
+constexpr uint16_t kRowEmpty = 0x00ffu;
+constexpr uint16_t kRowFull = (uint16_t)(15u << 8);
+
+template <int TH>
+__device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                              float Q, int tx, int ty, uint16_t* out, int stride) {
+    const float h00 = fmaf(-Q, r1.w, r2.z);
+    if (!(h00 > 0.0f) || !(Q < INFINITY)) {
+#pragma unroll
+        for (int rr = 0; rr < TH; ++rr) out[rr * stride] = kRowFull;
+        return;
+    }
+    const float h01 = 0.5f * fmaf(-Q, r2.x, r2.w);
+    const float h11 = fmaf(-Q, r2.y, r3.x);
+    const float hx = -Q * r1.y, hy2 = -2.0f * Q * r1.z, h22 = -Q * r1.x;
+    const float ih = 1.0f / h00;
+    const float uoff = r0.x - ((float)(tx * kTileW) + 0.5f);  // centre relative to tile column 0
+    const float row0 = (float)(ty * TH) + 0.5f;
+#pragma unroll
+    for (int rr = 0; rr < TH; ++rr) {
+        const float dv = ((row0 + (float)rr) - r0.z) - r0.w;
+        const float Bp = fmaf(h01, dv, hx);
+        const float Cp = fmaf(fmaf(h11, dv, hy2), dv, h22);
+        const float disc = fmaf(Bp, Bp, -h00 * Cp);
+        const float scale = fmaf(Bp, Bp, fabsf(h00 * Cp));
+        uint16_t code = kRowEmpty;
+        if (disc > -1e-3f * scale) {
+            const float w = sqrtf(fmaxf(disc, 0.0f)) * ih;
+            const float c = uoff - Bp * ih;
+            const float m = fmaf(0.02f, w, 1.0f);
+            const float klo = ceilf(c - w - m), khi = floorf(c + w + m);
+            const int lo = (int)fminf(fmaxf(klo, 0.0f), 16.0f);
+            const int hi = (int)fmaxf(fminf(khi, 15.0f), -1.0f);
+            if (lo <= hi) code = (uint16_t)(lo | (hi << 8));
+        }
+        out[rr * stride] = code;
     }
 }
 

@@ -99,11 +99,13 @@ template <int KM, int TH>
 __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
-    // phase 1 layout: stage[4][NT] float4 | sgid[NT] | skey[kSortMax] | sid[kSortMax]
+    // phase 1 layout: stage[4][NT] float4 | sgid[NT] | skey[kSortMax] | sid[kSortMax] | siv[TH][NT]
     float4* stage = smem;
     int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
     float* skey = reinterpret_cast<float*>(sgid + NT);
     int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
+    uint16_t* siv = reinterpret_cast<uint16_t*>(sid + kSortMax);
+    uint32_t* smask = reinterpret_cast<uint32_t*>(siv + TH * NT);  // [NT/32][NT] per-lane hit masks
     // phase 2 layout: jst[KM][NT] float4 (aliases phase 1)
     float4* jst = smem;
 
@@ -142,9 +144,11 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
             else g = base + tid;
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+            bool outside = false;
             if (src.filter_box) {
                 const int4 tb = a.ws.tbox[vb + g];
-                if (tx < tb.x || tx > tb.y || ty < tb.z || ty > tb.w) {
+                outside = tx < tb.x || tx > tb.y || ty < tb.z || ty > tb.w;
+                if (outside) {
                     r1 = make_float4(0.f, 0.f, 0.f, 0.f);
                     r2 = r1;
                 }
@@ -154,21 +158,74 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
             stage[2 * NT + tid] = r2;
             stage[3 * NT + tid] = r3;
             sgid[tid] = g;
+            if (outside) {
+#pragma unroll
+                for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;
+            } else {
+                row_intervals<TH>(r0, r1, r2, r3, a.Qeta, tx, ty, siv + tid, NT);
+            }
+        } else if (tid < ((nc + 3) & ~3)) {
+#pragma unroll
+            for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;  // pad the last group of four
         }
         __syncthreads();
         if (active) {
-            for (int q = 0; q < nc; ++q) {
-                const float4 r3 = stage[3 * NT + q];
-                if (src.mode == 1 && r3.w > key[KM - 1]) {
-                    active = false;  // sorted by lower bound: nothing later can enter
-                    break;
+            // 1) this pixel's hits in the chunk, as a bit mask (cheap, uniform)
+            constexpr int NW = NT / 32;
+            const int jl = tid & 15, rr = tid >> 4;
+            const uint2* ivrow = reinterpret_cast<const uint2*>(siv + rr * NT);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                uint32_t m = 0;
+#pragma unroll
+                for (int g4 = 0; g4 < 8; ++g4) {
+                    const int q0 = w * 32 + g4 * 4;
+                    if (q0 < nc) {
+                        const uint2 iv4 = ivrow[q0 >> 2];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t iv = ((u < 2 ? iv4.x : iv4.y) >> (16 * (u & 1))) & 0xffffu;
+                            m |= (jl >= (int)(iv & 255u) && jl <= (int)(iv >> 8)) ? (1u << (g4 * 4 + u)) : 0u;
+                        }
+                    }
                 }
-                const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q];
-                const float l = candidate_key(r0, r1, r2, r3, px, py, a.Qeta);
-                if (l > 0.0f) {
-                    const int32_t g = sgid[q];
-                    if (l < key[KM - 1] || (l == key[KM - 1] && g < id[KM - 1])) topk_insert<KM>(key, id, l, g);
+                smask[w * NT + tid] = m;
+            }
+            // 2) each lane walks its own hits: lanes of a warp trace different
+            //    candidates at the same time instead of the union of all hits
+            const float* lmin = reinterpret_cast<const float*>(stage + 3 * NT) + 3;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                uint32_t m = active ? smask[w * NT + tid] : 0u;
+                while (m) {
+                    const int q = w * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (src.mode == 1 && lmin[4 * q] > key[KM - 1]) {
+                        active = false;  // sorted by lower bound: nothing later can enter
+                        m = 0;
+                        break;
+                    }
+                    const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q], r3 = stage[3 * NT + q];
+                    const float l = candidate_key(r0, r1, r2, r3, px, py, a.Qeta);
+                    if (l > 0.0f) {
+                        const int32_t g = sgid[q];
+                        if (l < key[KM - 1] || (l == key[KM - 1] && g < id[KM - 1])) {
+                            if (l > key[KM - 2] || (l == key[KM - 2] && g > id[KM - 2])) {
+                                key[KM - 1] = l;  // lands last
+                                id[KM - 1] = g;
+                            } else {
+                                topk_insert<KM>(key, id, l, g);
+                            }
+                        }
+                    }
                 }
+            }
+            // a pixel whose list is full and whose next candidate (in sorted
+            // order) starts beyond its K-th depth can stop for good
+            if (active && src.mode == 1 && nc == NT && base + NT < src.count) {
+                // the first candidate of the next chunk bounds everything after it
+                const float nxt = skey[base + NT];
+                if (nxt > key[KM - 1]) active = false;
             }
         }
         if (__syncthreads_and(!active)) break;
@@ -176,21 +233,24 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
     __syncthreads();  // staging area becomes the j-stream
 
     // ---------------- fine pass ----------------
-    float hi[KM], lo[KM], A[KM];
+    // kept entries occupy slots [KM - K, KM - K + n) in ascending (l, index)
     int n = 0;
+#pragma unroll
+    for (int s = 0; s < KM; ++s) n += (valid && s >= KM - K && key[s] < INFINITY) ? 1 : 0;
+    float hi[KM], lo[KM], A[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s) {
         hi[s] = 0.0f;
         lo[s] = 0.0f;
         A[s] = 0.0f;
-        if (valid && s >= KM - K && key[s] < INFINITY) {
+        const int e = s - (KM - K);
+        if (e >= 0 && e < n) {
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + id[s], r0, r1, r2, r3);
-            const Entry e = entry_px(r0, r1, r2, r3, px, py);
-            hi[s] = e.hi;
-            lo[s] = e.lo;
-            jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
-            ++n;
+            const Entry en = entry_px(r0, r1, r2, r3, px, py);
+            hi[s] = en.hi;
+            lo[s] = en.lo;
+            jst[e * NT + tid] = make_float4(en.hi, en.lo, en.r, 0.5f * en.a);
         }
     }
     for (int e = 0; e < n; ++e) {
@@ -203,38 +263,82 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
         }
     }
-    if (!valid) return;
-
     const float ntl = -a.tau * kLog2e;
     float Wt[KM];
-    int e = 0;
+    {
+        int e = 0;
 #pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        Wt[s] = 0.0f;
-        if (s >= KM - K && key[s] < INFINITY) {
-            const float am = jst[e * NT + tid].w;
-            Wt[s] = ex2_approx(ntl * A[s]) * (2.0f * am);
-            ++e;
+        for (int s = 0; s < KM; ++s) {
+            Wt[s] = 0.0f;
+            if (s >= KM - K && s - (KM - K) < n) {
+                const float am = jst[e * NT + tid].w;
+                Wt[s] = ex2_approx(ntl * A[s]) * (2.0f * am);
+                ++e;
+            }
         }
     }
-    // outputs: weights / index in list order, image = sum W_k c_k
-    const int L = a.L;
+    // ---------------- outputs ----------------
+    // Each warp covers two 16-pixel row segments of the tile; a segment's
+    // lists are contiguous in memory ([pixel][L]).  The warp stages its 32
+    // lists in the shared-memory columns its own lanes used for the j-stream
+    // (blocks of 32 float4, one per list slot e) and writes each segment with
+    // consecutive lanes on consecutive words.
+    const int L = a.L, C = a.C;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nblk = (L + 3) >> 2;  // blocks of 128 words holding 32 x L entries
+    auto stg = [&](int x) -> float* { return reinterpret_cast<float*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127); };
+    __syncwarp();
 #pragma unroll
     for (int s = 0; s < KM; ++s) {
         if (s >= KM - K) {
             const int k = s - (KM - K);
-            const bool real = key[s] < INFINITY;
-            a.index[pix * L + k] = real ? id[s] : -1;
-            if (a.weights) a.weights[pix * L + k] = Wt[s];
+            const bool real = k < n;
+            *reinterpret_cast<int32_t*>(stg(lane * L + k)) = real ? id[s] : -1;
+            *stg(nblk * 128 + lane * L + k) = Wt[s];
         }
     }
-    const int C = a.C;
-    for (int c = 0; c < C; ++c) {
-        float acc = 0.0f;
+    __syncwarp();
+    {
+        const int ncols = min(kTileW, W - tx * kTileW);
 #pragma unroll
-        for (int s = 0; s < KM; ++s)
-            if (s >= KM - K && key[s] < INFINITY) acc = fmaf(Wt[s], __ldg(a.attr + (int64_t)id[s] * C + c), acc);
-        a.image[pix * C + c] = acc;
+        for (int rw = 0; rw < 2; ++rw) {
+            const int irow = ty * TH + 2 * warp + rw;
+            if (irow >= H) continue;
+            const int64_t first = __ldg(&cams[v].pix_base) + (int64_t)irow * W + tx * kTileW;
+            const int cnt = ncols * L;
+            int32_t* di = a.index + first * L;
+            float* dw = a.weights ? a.weights + first * L : nullptr;
+            for (int x = lane; x < cnt; x += 32) {
+                di[x] = *reinterpret_cast<const int32_t*>(stg(rw * 16 * L + x));
+                if (dw) dw[x] = *stg(nblk * 128 + rw * 16 * L + x);
+            }
+        }
+    }
+    if (C >= 16) {
+        // wide attributes: the warp blends one pixel at a time, lanes over channels
+        for (int p = 0; p < 32; ++p) {
+            const int irow = ty * TH + 2 * warp + (p >> 4), jcol = tx * kTileW + (p & 15);
+            if (irow >= H || jcol >= W) continue;
+            const int64_t pp = __ldg(&cams[v].pix_base) + (int64_t)irow * W + jcol;
+            for (int c0 = 0; c0 < C; c0 += 32) {
+                const int c = c0 + lane;
+                float acc = 0.0f;
+                for (int k = 0; k < L; ++k) {
+                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(p * L + k));
+                    if (g < 0) break;
+                    if (c < C) acc = fmaf(*stg(nblk * 128 + p * L + k), __ldg(a.attr + (int64_t)g * C + c), acc);
+                }
+                if (c < C) a.image[pp * C + c] = acc;
+            }
+        }
+    } else if (valid) {
+        for (int c = 0; c < C; ++c) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int s = 0; s < KM; ++s)
+                if (s >= KM - K && s - (KM - K) < n) acc = fmaf(Wt[s], __ldg(a.attr + (int64_t)id[s] * C + c), acc);
+            a.image[pix * C + c] = acc;
+        }
     }
 }
 
@@ -354,7 +458,8 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
 
 size_t render_smem_bytes(int KM, int TH) {
     const int NT = 16 * TH;
-    const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)kSortMax * 8;
+    const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)kSortMax * 8 + (size_t)NT * TH * 2 +
+                          (size_t)NT * (NT / 32) * 4;
     const size_t phase2 = (size_t)KM * NT * 16;
     return phase1 > phase2 ? phase1 : phase2;
 }

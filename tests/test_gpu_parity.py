@@ -136,7 +136,8 @@ def test_ragged_sizes_and_mixed_views():
     inv_cov = r32(scenes.inverse_covariance(scenes.random_rotations(rng, N),
                                             np.exp(rng.normal(np.log(0.08), 0.3, (N, 3)))))
     attr = r32(rng.uniform(0, 1, (N, 2)))
-    R2, _ = oracle.pose_to_RT([0.05, 0.02, 0.0, 0.0])
+    c, s = np.cos(0.1), np.sin(0.1)
+    R2 = np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])  # small turn about the vertical axis
     cams = [_cam(37, 53, 40.0), _cam(16, 16, 18.0), _cam(61, 29, 33.0, R=r32(R2), T=r32([0.1, -0.1, 0.2]))]
     *_, res = _run_full(cams, means, inv_cov, attr, K=12, tau=0.7, eta=0.005)
     assert res["covered"] > 500
