@@ -177,6 +177,33 @@ int voge_mse_grad(const float* image, const float* target, int64_t count, float*
                   voge_stream_t stream);
 
 /*
+ * Forward render that allocates nothing and takes no workspace.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory where they render (code inside a region that
+ * forbids cudaMalloc, such as a host callback or a real-time loop with a
+ * memory budget fixed up front, or a program that links only this library
+ * and has no allocator of its own).
+ *
+ * It behaves as voge_render_fwd (same arguments and outputs, minus the
+ * workspace) but uses a workspace of VOGE_STATIC_WORKSPACE_BYTES that lives
+ * in the library: a device array that every GPU loading libvoge.so holds
+ * until the process exits.
+ *   - Returns VOGE_ERR_WORKSPACE, and launches nothing, if
+ *     voge_workspace_bytes(cams, p) exceeds VOGE_STATIC_WORKSPACE_BYTES.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (each call clears what must start at zero).  Calls whose
+ *     work overlaps on the GPU -- for example on two streams -- race on it:
+ *     order them on one stream or synchronise between them.
+ *   - The caller still provides every input and output buffer (device).
+ */
+#define VOGE_STATIC_WORKSPACE_BYTES (32u << 20)
+int voge_render_fwd_static(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                           const float* attr, float* image, float* weights, int32_t* index, voge_stream_t stream);
+
+/*
  * One Adam step over `count` floats, in place (the optimiser of the paper's
  * shape fitting, Sec. 4.3):  m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
  * param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).

@@ -75,6 +75,8 @@ def lib():
             L.voge_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, ctypes.c_float, ctypes.c_int32, vp]
             L.voge_adam_step.restype = ctypes.c_int
+            L.voge_render_fwd_static.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp]
+            L.voge_render_fwd_static.restype = ctypes.c_int
             L.voge_trace_enable.argtypes = [ctypes.c_int]
             L.voge_trace_enable.restype = ctypes.c_int
             L.voge_trace_read.argtypes = [P(voge_trace_entry), ctypes.c_int]
@@ -159,6 +161,15 @@ def voge_render_bwd(cams, params, means, inv_cov, attr, index, grad_image, grad_
                                _ptr(grad_inv_cov, f32), _ptr(grad_attr, f32), _ptr(grad_cam, f32),
                                _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "voge_render_bwd")
+
+
+def voge_render_fwd_static(cams, params, means, inv_cov, attr, image, weights, index, stream=None):
+    """voge_render_fwd without a workspace argument (library-held workspace; see include/voge.h)."""
+    f32, i32 = torch.float32, torch.int32
+    rc = lib().voge_render_fwd_static(cams, ctypes.byref(params), _ptr(means, f32), _ptr(inv_cov, f32),
+                                      _ptr(attr, f32), _ptr(image, f32), _ptr(weights, f32), _ptr(index, i32),
+                                      _stream(stream))
+    _check(rc, "voge_render_fwd_static")
 
 
 def voge_pose_to_RT(pose):
