@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -182,6 +184,90 @@ def run_reference(args):
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------- serving ---
+def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
+    """Poisson render-and-compare requests (mean gap 2 ms) against resident scenes.
+
+    Scene pool: for each attribute width C in {3, 16, 128}, four scenes with N
+    drawn from U[1k, 100k] (the 8-view generator's distribution).  Each request
+    picks side in {128, 256, 512}, K in {10, 20, 32}, a scene of its C and a
+    random camera on the view sphere; it returns the loss and the gradients of
+    the means and the camera into pinned host memory."""
+    import threading
+
+    import torch
+
+    from paper_2205_15401_gb300 import scenes
+    from paper_2205_15401_gb300 import voge
+
+    rng = np.random.default_rng(seed)
+    srv = voge.Server(mem_budget_bytes=48 << 30, max_slots=256, use_graphs=batching, batching=batching,
+                      inflight_ticks=2 if batching else 1)
+    pool = {}
+    for C in (3, 16, 128):
+        pool[C] = []
+        for q in range(4):
+            N = int(rng.integers(1000, 100_001))
+            sc = scenes.fit_8x512(seed=1000 + 10 * C + q, N=N, B=1, side=16, C=C)
+            pool[C].append((srv.add_scene(sc["means"], sc["inv_cov"], sc["attr"]), N))
+    targets = {(side, C): torch.rand((side * side, C)).pin_memory() for side in (128, 256, 512) for C in (3, 16, 128)}
+    out_pool = [{"grad_means": torch.empty((100_001, 3)).pin_memory(), "grad_cam": torch.empty(12).pin_memory(),
+                 "loss": torch.empty(1).pin_memory()} for _ in range(512)]
+    stream = scenes.serving_stream(seed=seed, duration_s=warmup_s + seconds)
+    done, lock = [], threading.Lock()
+    tickets = []
+    cv = threading.Condition()
+
+    def consumer():
+        k = 0
+        while True:
+            with cv:
+                while k >= len(tickets):
+                    cv.wait()
+                item = tickets[k]
+            if item is None:
+                return
+            t, px, arrive = item
+            rc, tm = srv.wait(t, -1)
+            with lock:
+                done.append((arrive, tm, px, rc))
+            k += 1
+
+    th = threading.Thread(target=consumer)
+    th.start()
+    t0 = time.perf_counter()
+    for q, req in enumerate(stream):
+        delay = req["t"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        sid, N = pool[req["C"]][int(rng.integers(0, 4))]
+        side = req["side"]
+        pose = [rng.uniform(-np.pi, np.pi), rng.uniform(-1.0, 1.0), 4.0, 0.0]
+        R, T = voge.voge_pose_to_RT(pose)
+        cam = {"R": R, "T": T, "F": float(side), "Ox": side / 2, "Oy": side / 2, "H": side, "W": side}
+        rc, t = srv.submit(cam, targets[(side, req["C"])], req["K"], thresh=0.01, scene=sid,
+                           outputs=out_pool[q % len(out_pool)])
+        if rc == 0:
+            with cv:
+                tickets.append((t, side * side, req["t"]))
+                cv.notify()
+    with cv:
+        tickets.append(None)
+        cv.notify()
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    meas = [(tm, px) for arrive, tm, px, rc in done if rc == 0 and arrive >= warmup_s]
+    lat = np.array([tm["done_us"] - tm["submit_us"] for tm, _ in meas]) / 1e3
+    t_first = min(tm["submit_us"] for tm, _ in meas)
+    t_last = max(tm["done_us"] for tm, _ in meas)
+    mpix = sum(px for _, px in meas) / ((t_last - t_first) / 1e6) / 1e6
+    return {"requests": len(meas), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "mpix_s": mpix, "ticks": stats["ticks"],
+            "requests_per_tick": stats["requests_in_ticks"] / max(stats["ticks"], 1),
+            "rejected": stats["rejected"], "graphs": stats["graphs_captured"]}
 
 
 # --------------------------------------------------------------- GPU path ---
@@ -394,6 +480,14 @@ def main():
         plain = {"value": P / (pms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": pms,
                  "what": "same step, every pixel tests every Gaussian (no tile binning)"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        batched = serving_bench(dev, args.serving_seconds, True, seed=args.seed)
+        plain_srv = serving_bench(dev, args.serving_seconds, False, seed=args.seed)
+        serving = {"workload": "Poisson arrivals, mean gap 2 ms, 1 s warm-up then measured; N U[1k,100k] "
+                               "(resident scenes), side {128,256,512}, C {3,16,128}, K {10,20,32}",
+                   "batched": batched, "plain": plain_srv}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -410,6 +504,7 @@ def main():
                           **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
                           "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+               "serving": serving,
                "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:

@@ -176,6 +176,112 @@ int voge_pose_grad(const float* pose, const float* grad_cam, float* grad_pose, i
 int voge_mse_grad(const float* image, const float* target, int64_t count, float* grad_image, float* loss,
                   voge_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: render-and-compare requests with continuous batching.
+ *
+ * Not a step of the paper: the paper's analysis-by-synthesis loops (pose
+ * estimation, Sec. 4.1; shape fitting, Sec. 4.3) issue one render + gradient
+ * per optimisation step.  The server runs many such steps for many scenes at
+ * once.  A request renders one view of its own scene (voge_render_fwd), takes
+ * the mean squared error against a target image and returns the image, the
+ * loss and the gradients (voge_render_bwd), exactly as those calls would.
+ *
+ * Requests are admitted in arrival order whenever a slot and enough of the
+ * server's device memory are free; their inputs are copied in on a copy
+ * stream while earlier work runs.  Each tick takes every admitted request
+ * whose inputs have arrived and runs them together: one persistent launch
+ * per list-length class covers all of them.  With use_graphs, a tick is the
+ * replay of a CUDA graph captured once per set of classes present.  Up to
+ * inflight_ticks ticks run at once on separate streams.  With batching = 0
+ * every request runs alone (one request per tick): the plain comparator.
+ *
+ * Ownership: the server allocates its device memory (mem_budget_bytes, one
+ * allocation) and pinned staging at creation, and nothing afterwards.  Host
+ * buffers of a request (inputs and outputs) must stay valid until
+ * voge_server_wait returns for its ticket; page-locked host buffers keep the
+ * copies asynchronous (pageable ones make the scheduler thread wait).
+ * ------------------------------------------------------------------------ */
+typedef struct voge_server voge_server;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t max_slots;         /* requests resident on the device at once (>= 1) */
+    int32_t max_queue;         /* pending requests before submit returns VOGE_ERR_BUSY (<= 0: 65536) */
+    int32_t use_graphs;        /* 1: each tick is a CUDA-graph replay */
+    int32_t batching;          /* 1: continuous batching; 0: one request per tick */
+    int32_t inflight_ticks;    /* ticks running at once, 1..4 (<= 0: 2) */
+    int64_t max_tick_gaussians;/* Gaussians summed over one tick's requests (<= 0: what a quarter of
+                                  the budget holds, between 64 Ki and 4 Mi) */
+    int64_t max_tick_pixels;   /* pixels summed over one tick's requests (<= 0: 16 Mi) */
+    size_t mem_budget_bytes;   /* device memory of the server (>= 1 MiB) */
+} voge_server_config;
+
+typedef struct {
+    voge_camera cam;           /* the view to render */
+    int32_t scene;             /* resident scene id (voge_server_add_scene), or -1: parameters below */
+    int32_t N, C, K;           /* Gaussians, attribute channels (ignored for a resident scene), list
+                                  length (K <= 32 once clipped to N) */
+    float tau, thresh;         /* as voge_params */
+    const float* means;        /* host [N][3] (inline scene only) */
+    const float* inv_cov;      /* host [N][6] (inline scene only) */
+    const float* attr;         /* host [N][C] (inline scene only) */
+    const float* target;       /* host [H][W][C]: the image to match */
+    float* image;              /* host [H][W][C] out, or NULL */
+    float* grad_means;         /* host [N][3] out (dLoss/dmeans), or NULL */
+    float* grad_inv_cov;       /* host [N][6] out, or NULL */
+    float* grad_attr;          /* host [N][C] out, or NULL */
+    float* grad_cam;           /* host [12] out: dLoss/dR (row-major), dLoss/dT, or NULL */
+    float* loss;               /* host [1] out: mean squared error, or NULL */
+} voge_request;
+
+typedef struct {
+    double submit_us, admit_us, start_us, done_us; /* server clock, microseconds */
+    int32_t tick;              /* tick the request ran in */
+    int32_t status;            /* VOGE_OK or the error that ended it */
+} voge_request_timing;
+
+typedef struct {
+    int64_t submitted, completed, rejected, ticks, requests_in_ticks, graphs_captured, queued;
+    int32_t resident, pad;
+} voge_server_stats;
+
+/* Create a server (allocates its device memory and starts its scheduler
+ * thread).  VOGE_ERR_ARG for a bad config, VOGE_ERR_ADMISSION if the budget
+ * cannot hold the tick workspaces, VOGE_ERR_CUDA on a CUDA failure. */
+int voge_server_create(const voge_server_config* cfg, voge_server** out);
+
+/* Queue a request (host descriptor copied; buffers referenced).  *ticket
+ * identifies it.  VOGE_ERR_ADMISSION if it can never fit the server,
+ * VOGE_ERR_BUSY if the queue is full, VOGE_ERR_UNSUPPORTED for lists longer
+ * than 32, VOGE_ERR_ARG for invalid fields. */
+int voge_server_submit(voge_server* s, const voge_request* req, uint64_t* ticket);
+
+/* Wait until the request's outputs are in its host buffers.  timeout_ms < 0
+ * waits without limit; on timeout returns VOGE_ERR_TIMEOUT and the ticket
+ * stays valid.  Otherwise returns the request's status and retires the ticket;
+ * `timing` (may be NULL) receives its timestamps. */
+int voge_server_wait(voge_server* s, uint64_t ticket, int32_t timeout_ms, voge_request_timing* timing);
+
+/* Copy a scene into the server's memory once; requests then name it by
+ * *scene_id instead of sending its parameters.  Host arrays may be freed on
+ * return.  VOGE_ERR_ADMISSION if it does not fit. */
+int voge_server_add_scene(voge_server* s, int32_t N, int32_t C, const float* means, const float* inv_cov,
+                          const float* attr, int32_t* scene_id);
+
+/* Free a resident scene; VOGE_ERR_BUSY while a request that uses it is pending. */
+int voge_server_remove_scene(voge_server* s, int32_t scene_id);
+
+/* Hold (paused = 1) or release (0) the start of new ticks.  Admission and
+ * input copies go on while held, so releasing starts one tick over every
+ * request admitted meanwhile. */
+int voge_server_pause(voge_server* s, int32_t paused);
+
+/* Counters of the server (host memory). */
+int voge_server_get_stats(voge_server* s, voge_server_stats* out);
+
+/* Finish the queued work, stop the scheduler and free everything. */
+int voge_server_destroy(voge_server* s);
+
 /*
  * Forward render that allocates nothing and takes no workspace.  The paper
  * has no counterpart: this entry point exists for callers that cannot

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/voge.h"
@@ -10,11 +11,36 @@
 #include "voge_trace.cuh"
 
 namespace voge {
-cudaError_t launch_project(int64_t BN, int count_tiles, cudaStream_t s, const Args& a);
+cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
-cudaError_t launch_grad_finalize(int N, cudaStream_t s, const Args& a, float* grad_means, float* grad_inv_cov,
-                                 float* grad_cam);
+cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a);
+int render_blocks_per_sm(int KM);
+int backward_blocks_per_sm(int KM);
+
+// Persistent tile launches: as many CTAs as can be resident at once (cached
+// per device and variant), never more than there are tiles.
+int tile_grid(int KM, int fwd, int total_tiles) {
+    static std::mutex mu;
+    static int cache[64][2][6];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const int vi = KM == 8 ? 0 : KM == 16 ? 1 : KM == 20 ? 2 : KM == 24 ? 3 : KM == 32 ? 4 : 5;
+    int g;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        g = cache[dev][fwd ? 1 : 0][vi];
+    }
+    if (g == 0) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+        g = nsm * (fwd ? render_blocks_per_sm(KM) : backward_blocks_per_sm(KM));
+        std::lock_guard<std::mutex> lk(mu);
+        cache[dev][fwd ? 1 : 0][vi] = g;
+    }
+    return total_tiles < g ? total_tiles : g;
+}
 }  // namespace voge
 
 using namespace voge;
@@ -41,9 +67,9 @@ void pick_variant(int L, int* KM, int* TH) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cams, rec, rec2, tbox, tile_cnt, tile_off, tile_cur, tile_gauss, gcam, gkey, gid, total;
+    size_t desc, rec, rec2, tbox, tile_cnt, tile_off, tile_cur, tile_gauss, gcam, gkey, gid, total;
     int64_t pixels, bin_cap;
-    int32_t total_tiles, TH, KM;
+    int32_t total_tiles, TH, KM, L;
 };
 
 bool valid_params(const voge_camera* cams, const voge_params* p) {
@@ -64,8 +90,8 @@ bool valid_params(const voge_camera* cams, const voge_params* p) {
 
 Layout make_layout(const voge_camera* cams, const voge_params* p) {
     Layout l;
-    const int L = list_length(p);
-    pick_variant(L, &l.KM, &l.TH);
+    l.L = list_length(p);
+    pick_variant(l.L, &l.KM, &l.TH);
     int64_t tiles = 0, pixels = 0;
     for (int v = 0; v < p->B; ++v) {
         const int tx = (cams[v].W + kTileW - 1) / kTileW, ty = (cams[v].H + l.TH - 1) / l.TH;
@@ -79,7 +105,7 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.bin_cap = BN * cap;
     if (l.bin_cap > (int64_t)INT32_MAX) l.bin_cap = INT32_MAX;
     size_t o = 0;
-    l.cams = o; o = align256(o + sizeof(CamDev) * p->B);
+    l.desc = o; o = align256(o + sizeof(BatchHdr) + sizeof(ViewDesc) * p->B);
     l.rec = o; o = align256(o + 64 * (size_t)BN);
     l.rec2 = o; o = align256(o + 32 * (size_t)BN);
     l.tbox = o; o = align256(o + 16 * (size_t)BN);
@@ -88,9 +114,9 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.tile_cur = o; o = align256(o + 4 * (size_t)(tiles + 1));
     l.tile_gauss = o; o = align256(o + 4 * (size_t)l.bin_cap);
     l.gcam = o; o = align256(o + 36 * (size_t)BN);
-    if (l.KM == 0 && L > 0) {
-        l.gkey = o; o = align256(o + 32 * (size_t)pixels * L);  // 8 floats per entry (backward scratch)
-        l.gid = o; o = align256(o + 4 * (size_t)pixels * L);
+    if (l.KM == 0 && l.L > 0) {
+        l.gkey = o; o = align256(o + 32 * (size_t)pixels * l.L);  // 8 floats per entry
+        l.gid = o; o = align256(o + 4 * (size_t)pixels * l.L);
     } else {
         l.gkey = l.gid = o;
     }
@@ -101,7 +127,6 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
 Ws make_ws(const Layout& l, void* base) {
     char* b = static_cast<char*>(base);
     Ws w;
-    w.cams = reinterpret_cast<CamDev*>(b + l.cams);
     w.rec = reinterpret_cast<float4*>(b + l.rec);
     w.rec2 = reinterpret_cast<float4*>(b + l.rec2);
     w.tbox = reinterpret_cast<int4*>(b + l.tbox);
@@ -113,17 +138,32 @@ Ws make_ws(const Layout& l, void* base) {
     w.gcam = reinterpret_cast<float*>(b + l.gcam);
     w.gkey = reinterpret_cast<float*>(b + l.gkey);
     w.gid = reinterpret_cast<int32_t*>(b + l.gid);
-    w.total_tiles = l.total_tiles;
+    w.gen_L = l.L;
     return w;
 }
 
-void build_cams(const voge_camera* cams, const voge_params* p, int TH, std::vector<CamDev>& out) {
-    out.resize(p->B);
+struct Buffers {
+    const float *means, *inv_cov, *attr;
+    float *image, *weights;
+    int32_t* index;
+    const int32_t* index_in;
+    const float* grad_image;
+    float *grad_means, *grad_inv_cov, *grad_attr, *grad_cam;
+};
+
+// View table of a render call: every view shares the scene; outputs are
+// laid out view after view.
+void build_views(const voge_camera* cams, const voge_params* p, const Layout& l, const Buffers& b,
+                 std::vector<unsigned char>& blob) {
+    blob.assign(sizeof(BatchHdr) + sizeof(ViewDesc) * p->B, 0);
+    BatchHdr* h = reinterpret_cast<BatchHdr*>(blob.data());
+    ViewDesc* vd = reinterpret_cast<ViewDesc*>(blob.data() + sizeof(BatchHdr));
+    const int use_thresh = p->thresh > 0.0f ? 1 : 0;
+    const float Qeta = use_thresh ? (p->thresh >= 1.0f ? 0.0f : (float)(2.0 * log(1.0 / (double)p->thresh))) : INFINITY;
     int32_t tile_base = 0;
     int64_t pix_base = 0;
     for (int v = 0; v < p->B; ++v) {
-        CamDev& d = out[v];
-        memset(&d, 0, sizeof(d));
+        ViewDesc& d = vd[v];
         memcpy(d.R, cams[v].R, sizeof(d.R));
         memcpy(d.T, cams[v].T, sizeof(d.T));
         d.F = cams[v].F;
@@ -133,44 +173,74 @@ void build_cams(const voge_camera* cams, const voge_params* p, int TH, std::vect
         d.H = cams[v].H;
         d.W = cams[v].W;
         d.tiles_x = (cams[v].W + kTileW - 1) / kTileW;
-        d.tiles_y = (cams[v].H + TH - 1) / TH;
-        d.tile_h = TH;
+        d.tiles_y = (cams[v].H + l.TH - 1) / l.TH;
+        d.tile_h = l.TH;
         d.tile_base = tile_base;
+        d.N = p->N;
+        d.C = p->C;
+        d.L = l.L;
+        d.use_thresh = use_thresh;
+        d.plain = (p->flags & VOGE_FLAG_PLAIN) ? 1 : 0;
+        d.tau = p->tau;
+        d.Qeta = Qeta;
+        d.rec_base = (int64_t)v * p->N;
         d.pix_base = pix_base;
+        d.elem_base = pix_base * p->C;
+        d.means = b.means;
+        d.inv_cov = b.inv_cov;
+        d.attr = b.attr;
+        d.image = b.image ? b.image + pix_base * p->C : nullptr;
+        d.weights = b.weights ? b.weights + pix_base * l.L : nullptr;
+        d.index = b.index ? b.index + pix_base * l.L : nullptr;
+        d.index_in = b.index_in ? b.index_in + pix_base * l.L : nullptr;
+        d.grad_image = b.grad_image ? b.grad_image + pix_base * p->C : nullptr;
+        d.grad_means = b.grad_means;
+        d.grad_inv_cov = b.grad_inv_cov;
+        d.grad_attr = b.grad_attr;
+        d.grad_cam = b.grad_cam ? b.grad_cam + 12 * v : nullptr;
         tile_base += d.tiles_x * d.tiles_y;
         pix_base += (int64_t)cams[v].H * cams[v].W;
     }
+    h->total_records = (int64_t)p->B * p->N;
+    h->total_elems = pix_base * p->C;
+    h->total_tiles = tile_base;
+    h->nviews = p->B;
+    h->class_begin[0] = 0;
+    h->class_end[0] = tile_base;
+    h->shared_scene = 1;
 }
 
-Args make_args(const voge_params* p, const Layout& l, void* ws) {
+Args make_args(const Layout& l, void* ws) {
     Args a;
     memset(&a, 0, sizeof(a));
-    a.B = p->B;
-    a.N = p->N;
-    a.C = p->C;
-    a.K = p->K;
-    a.L = list_length(p);
-    a.tau = p->tau;
-    a.use_thresh = p->thresh > 0.0f ? 1 : 0;
-    a.Qeta = a.use_thresh ? (p->thresh >= 1.0f ? 0.0f : (float)(2.0 * log(1.0 / (double)p->thresh))) : INFINITY;
-    a.plain = (p->flags & VOGE_FLAG_PLAIN) ? 1 : 0;
+    char* b = static_cast<char*>(ws);
+    a.hdr = reinterpret_cast<BatchHdr*>(b + l.desc);
+    a.views = reinterpret_cast<const ViewDesc*>(b + l.desc + sizeof(BatchHdr));
     a.ws = make_ws(l, ws);
+    a.cls = 0;
     return a;
 }
 
-// Upload cameras and project every (view, Gaussian); with `bin` also build
-// the tile lists.
-int project_and_bin(const voge_camera* cams, const voge_params* p, const Layout& l, const Args& a, int bin,
-                    cudaStream_t s) {
-    std::vector<CamDev> cd;
-    build_cams(cams, p, l.TH, cd);
-    if (cudaMemcpyAsync(a.ws.cams, cd.data(), sizeof(CamDev) * p->B, cudaMemcpyHostToDevice, s) != cudaSuccess)
+int record_grid(int64_t records) {
+    int64_t g = (records + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Upload the view table and header, project every (view, Gaussian); with
+// `bin` also build the tile lists.
+int upload_and_project(const voge_camera* cams, const voge_params* p, const Layout& l, const Args& a,
+                       const Buffers& b, int project, int bin, cudaStream_t s) {
+    std::vector<unsigned char> blob;
+    build_views(cams, p, l, b, blob);
+    if (cudaMemcpyAsync(a.hdr, blob.data(), blob.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return VOGE_ERR_CUDA;
-    const int64_t BN = (int64_t)p->B * p->N;
-    const int count_tiles = bin && !a.plain;
+    if (!project) return VOGE_OK;
+    const int count_tiles = bin && !(p->flags & VOGE_FLAG_PLAIN);
     if (count_tiles && cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(l.total_tiles + 1), s) != cudaSuccess)
         return VOGE_ERR_CUDA;
-    return launch_project(BN, count_tiles, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+    return launch_project(record_grid((int64_t)p->B * p->N), count_tiles, s, a) == cudaSuccess ? VOGE_OK
+                                                                                                : VOGE_ERR_CUDA;
 }
 
 __global__ void k_pose_grad(const float* pose, const float* gcam, float* gpose, int B) {
@@ -274,17 +344,20 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
         return cudaMemsetAsync(image, 0, sizeof(float) * (size_t)l.pixels * p->C, s) == cudaSuccess ? VOGE_OK
                                                                                                     : VOGE_ERR_CUDA;
     }
-    Args a = make_args(p, l, workspace);
-    a.means = means;
-    a.inv_cov = inv_cov;
-    a.attr = attr;
-    a.image = image;
-    a.weights = weights;
-    a.index = index;
-    int rc = project_and_bin(cams, p, l, a, 1, s);
+    const Args a = make_args(l, workspace);
+    Buffers b;
+    memset(&b, 0, sizeof(b));
+    b.means = means;
+    b.inv_cov = inv_cov;
+    b.attr = attr;
+    b.image = image;
+    b.weights = weights;
+    b.index = index;
+    int rc = upload_and_project(cams, p, l, a, b, 1, 1, s);
     if (rc != VOGE_OK) return rc;
     if (l.total_tiles == 0) return VOGE_OK;
-    return launch_render_tiles(l.KM, l.total_tiles, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+    return launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a) == cudaSuccess ? VOGE_OK
+                                                                                              : VOGE_ERR_CUDA;
 }
 
 int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
@@ -298,21 +371,26 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
     const Layout l = make_layout(cams, p);
     if (!workspace || workspace_bytes < l.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
         return VOGE_ERR_WORKSPACE;
-    Args a = make_args(p, l, workspace);
-    a.means = means;
-    a.inv_cov = inv_cov;
-    a.attr = attr;
-    a.index_in = index;
-    a.grad_image = grad_image;
-    a.grad_attr = grad_attr;
-    if (!(p->flags & VOGE_FLAG_REUSE_PROJECTION)) {
-        int rc = project_and_bin(cams, p, l, a, 0, s);
-        if (rc != VOGE_OK) return rc;
-    }
-    const bool geo = grad_means || grad_inv_cov || grad_cam;
+    const Args a = make_args(l, workspace);
+    Buffers b;
+    memset(&b, 0, sizeof(b));
+    b.means = means;
+    b.inv_cov = inv_cov;
+    b.attr = attr;
+    b.index_in = index;
+    b.grad_image = grad_image;
+    b.grad_means = grad_means;
+    b.grad_inv_cov = grad_inv_cov;
+    b.grad_attr = grad_attr;
+    b.grad_cam = grad_cam;
+    const int project = (p->flags & VOGE_FLAG_REUSE_PROJECTION) ? 0 : 1;
+    int rc = upload_and_project(cams, p, l, a, b, project, 0, s);
+    if (rc != VOGE_OK) return rc;
     if (cudaMemsetAsync(a.ws.gcam, 0, 36 * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
-    if (l.total_tiles > 0 && launch_backward_tiles(l.KM, l.total_tiles, s, a) != cudaSuccess) return VOGE_ERR_CUDA;
-    if (geo && launch_grad_finalize(p->N, s, a, grad_means, grad_inv_cov, grad_cam) != cudaSuccess)
+    if (l.total_tiles > 0 && launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a) != cudaSuccess)
+        return VOGE_ERR_CUDA;
+    if ((grad_means || grad_inv_cov || grad_cam) &&
+        launch_grad_finalize(record_grid(p->N), 1, s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
     return VOGE_OK;
 }

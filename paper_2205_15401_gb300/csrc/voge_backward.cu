@@ -56,31 +56,33 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, float 
 }
 
 template <int KM, int TH>
-__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) {
+__device__ __forceinline__ void backward_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     float4* jst = smem;  // [KM][NT]
 
-    const CamDev* cams = a.ws.cams;
-    const int t = blockIdx.x;
-    const int v = find_view(cams, a.B, t);
-    const int lt = t - __ldg(&cams[v].tile_base);
-    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int v = view_of_tile(a.views, a.hdr->nviews, t);
+    const ViewDesc& vd = a.views[v];
+    const int lt = t - vd.tile_base;
+    const int tiles_x = vd.tiles_x;
     const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
-    const float invF = __ldg(&cams[v].invF);
+    const int H = vd.H, W = vd.W;
+    const float invF = vd.invF;
     const int tid = threadIdx.x;
     const int j = tx * kTileW + (tid & 15);
     const int i = ty * TH + (tid >> 4);
     const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
-    const int64_t vb = (int64_t)v * a.N;
-    const int L = a.L, K = a.L, C = a.C;
+    const int64_t pix = (int64_t)i * W + j;
+    const int64_t vb = vd.rec_base;
+    const int L = vd.L, K = vd.L, C = vd.C, N = vd.N;
+    const float tau = vd.tau;
+    const float* attr = vd.attr;
+    float* grad_attr = vd.grad_attr;
 
     int32_t id[KM];
     float hi[KM], lo[KM], dA[KM], dl[KM];
-    if (!valid) return;  // no block-wide barriers in this kernel
+    if (!valid) return;  // no block-wide barriers inside a tile
     int n = 0;
     bool open = true;
 #pragma unroll
@@ -91,8 +93,8 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
         dA[s] = 0.0f;
         dl[s] = 0.0f;
         if (s >= KM - K && open) {
-            const int32_t g = __ldg(a.index_in + pix * L + (s - (KM - K)));
-            if (g >= 0 && g < a.N) {
+            const int32_t g = __ldg(vd.index_in + pix * L + (s - (KM - K)));
+            if (g >= 0 && g < N) {
                 float4 r0, r1, r2, r3;
                 load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
                 const Entry e = entry_px(r0, r1, r2, r3, px, py);
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
         }
     }
     // T, W, attribute gradient, dA
-    const float ntl = -a.tau * kLog2e;
-    const float* gp = a.grad_image + pix * C;
+    const float ntl = -tau * kLog2e;
+    const float* gp = vd.grad_image + pix * C;
     {
         int e = 0;
 #pragma unroll
@@ -130,14 +132,14 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
             if (id[s] >= 0) {
                 const float am = jst[e * NT + tid].w;
                 const float Wk = ex2_approx(ntl * A[s]) * (2.0f * am);
-                const float* ck = a.attr + (int64_t)id[s] * C;
+                const float* ck = attr + (int64_t)id[s] * C;
                 float G = 0.0f;
                 for (int c = 0; c < C; ++c) {
                     const float gc = __ldg(gp + c);
                     G = fmaf(gc, __ldg(ck + c), G);
-                    if (a.grad_attr) atomicAdd(a.grad_attr + (int64_t)id[s] * C + c, Wk * gc);
+                    if (grad_attr) atomicAdd(grad_attr + (int64_t)id[s] * C + c, Wk * gc);
                 }
-                dA[s] = -a.tau * G * Wk;
+                dA[s] = -tau * G * Wk;
                 ++e;
             }
         }
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
         jst[e * NT + tid] = make_float4(acc_dm, -acc_s * J.z, acc_dr, 0.0f);
     }
     // chain rule to camera space
-    const float inv2tau = 0.5f / a.tau;
+    const float inv2tau = 0.5f / tau;
     {
         int e = 0;
 #pragma unroll
@@ -187,32 +189,42 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
     }
 }
 
+template <int KM, int TH>
+__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) {
+    __shared__ int s_slot;
+    for (;;) {
+        const int t = next_tile(a, 0, &s_slot);
+        if (t < 0) return;
+        backward_tile<KM, TH>(a, t);
+    }
+}
+
 // Generic backward for list lengths above the register lists (L > 32).
 // Per-pixel scratch in the workspace: [L][8] floats = hi, lo, r, m, A->dA, dl, dm, dr.
-__global__ void __launch_bounds__(256) k_backward_generic(Args a) {
+__device__ __forceinline__ void backward_tile_generic(const Args& a, int t) {
     constexpr int TH = 16;
-    const CamDev* cams = a.ws.cams;
-    const int t = blockIdx.x;
-    const int v = find_view(cams, a.B, t);
-    const int lt = t - __ldg(&cams[v].tile_base);
-    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int v = view_of_tile(a.views, a.hdr->nviews, t);
+    const ViewDesc& vd = a.views[v];
+    const int lt = t - vd.tile_base;
+    const int tiles_x = vd.tiles_x;
     const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
-    const float invF = __ldg(&cams[v].invF);
+    const int H = vd.H, W = vd.W;
+    const float invF = vd.invF;
     const int tid = threadIdx.x;
     const int j = tx * kTileW + (tid & 15);
     const int i = ty * TH + (tid >> 4);
     if (i >= H || j >= W) return;
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
-    const int64_t vb = (int64_t)v * a.N;
-    const int L = a.L, C = a.C;
-    const int32_t* li = a.index_in + pix * L;
-    float* S = a.ws.gkey + pix * (int64_t)L * 8;
+    const int64_t pix = (int64_t)i * W + j;
+    const int64_t vb = vd.rec_base;
+    const int L = vd.L, C = vd.C;
+    const float tau = vd.tau;
+    const int32_t* li = vd.index_in + pix * L;
+    float* S = a.ws.gkey + (vd.pix_base + pix) * (int64_t)a.ws.gen_L * 8;
     int n = 0;
     while (n < L) {
         const int32_t g = li[n];
-        if (g < 0 || g >= a.N) break;
+        if (g < 0 || g >= vd.N) break;
         float4 r0, r1, r2, r3;
         load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
         const Entry e = entry_px(r0, r1, r2, r3, px, py);
@@ -221,7 +233,7 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a) {
         s[4] = 0.0f; s[5] = 0.0f; s[6] = 0.0f; s[7] = 0.0f;
         ++n;
     }
-    const float* gp = a.grad_image + pix * C;
+    const float* gp = vd.grad_image + pix * C;
     for (int k = 0; k < n; ++k) {
         float* sk = S + 8 * k;
         float A = 0.0f;
@@ -232,15 +244,15 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a) {
             const float sm = copysignf(sj[3], u);
             A = fmaf(-sm, q, A + (sj[3] + sm));
         }
-        const float Wk = ex2_approx(-a.tau * kLog2e * A) * (2.0f * sk[3]);
+        const float Wk = ex2_approx(-tau * kLog2e * A) * (2.0f * sk[3]);
         const int32_t g = li[k];
         float G = 0.0f;
         for (int c = 0; c < C; ++c) {
             const float gc = gp[c];
-            G = fmaf(gc, __ldg(a.attr + (int64_t)g * C + c), G);
-            if (a.grad_attr) atomicAdd(a.grad_attr + (int64_t)g * C + c, Wk * gc);
+            G = fmaf(gc, __ldg(vd.attr + (int64_t)g * C + c), G);
+            if (vd.grad_attr) atomicAdd(vd.grad_attr + (int64_t)g * C + c, Wk * gc);
         }
-        sk[4] = -a.tau * G * Wk;
+        sk[4] = -tau * G * Wk;
     }
     for (int k = 0; k < n; ++k) {
         float* sk = S + 8 * k;
@@ -258,7 +270,7 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a) {
             sj[7] = fmaf(du, d, sj[7]);
         }
     }
-    const float inv2tau = 0.5f / a.tau;
+    const float inv2tau = 0.5f / tau;
     for (int k = 0; k < n; ++k) {
         const float* sk = S + 8 * k;
         const float dqt = fmaf(sk[4], inv2tau, -0.5f * sk[3] * sk[6]);  // a/4 = m/2
@@ -270,79 +282,111 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a) {
     }
 }
 
-// Camera-space accumulators -> world-space gradients of means and inverse
-// covariances (M = R M_w + T, P = R P_w Rᵀ), and dL/dR = dM M_wᵀ + 2 G R P_w,
-// dL/dT = dM reduced over Gaussians per view.
-__global__ void __launch_bounds__(256) k_grad_finalize(Args a, float* grad_means, float* grad_inv_cov, float* grad_cam) {
-    __shared__ float red[8][12];
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = g < a.N;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float gm[3] = {0.f, 0.f, 0.f}, gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float Mw[3] = {0.f, 0.f, 0.f}, Pw[9];
-    if (live) {
-        for (int q = 0; q < 3; ++q) Mw[q] = __ldg(a.means + 3 * (int64_t)g + q);
-        const float* p6 = a.inv_cov + 6 * (int64_t)g;
-        Pw[0] = __ldg(p6 + 0); Pw[1] = __ldg(p6 + 1); Pw[2] = __ldg(p6 + 2);
-        Pw[3] = Pw[1]; Pw[4] = __ldg(p6 + 3); Pw[5] = __ldg(p6 + 4);
-        Pw[6] = Pw[2]; Pw[7] = Pw[5]; Pw[8] = __ldg(p6 + 5);
-    } else {
-        for (int q = 0; q < 9; ++q) Pw[q] = 0.0f;
+__global__ void __launch_bounds__(256) k_backward_generic(Args a) {
+    __shared__ int s_slot;
+    for (;;) {
+        const int t = next_tile(a, 0, &s_slot);
+        if (t < 0) return;
+        backward_tile_generic(a, t);
     }
-    for (int v = 0; v < a.B; ++v) {
-        float R[9];
-        for (int q = 0; q < 9; ++q) R[q] = __ldg(&a.ws.cams[v].R[q]);
-        float dM[3] = {0.f, 0.f, 0.f}, G[9];
-        for (int q = 0; q < 9; ++q) G[q] = 0.0f;
+}
+
+// Camera-space accumulators -> world-space gradients of each view's scene
+// (M = R M_w + T, P = R P_w Rᵀ): dM_w = Rᵀ dM, dP_w = Rᵀ G R, and the camera
+// pose dL/dR = dM M_wᵀ + 2 G R P_w, dL/dT = dM summed over the view's
+// Gaussians.  One thread per (view, Gaussian) record; the accumulators are
+// cleared once read.
+__global__ void __launch_bounds__(256) k_grad_finalize(Args a) {
+    const int nv = a.hdr->nviews;
+    const int64_t total = a.hdr->total_records;
+    const int lane = threadIdx.x & 31;
+    for (int64_t tb = (int64_t)blockIdx.x * blockDim.x; tb < total; tb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = tb + threadIdx.x;
+        const bool live = t < total;
+        const int v = live ? view_of_record(a.views, nv, t) : -1;
+        float p[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) p[q] = 0.0f;
+        float* gcam_out = nullptr;
         if (live) {
-            const float* gc = a.ws.gcam + 9 * ((int64_t)v * a.N + g);
-            dM[0] = gc[0]; dM[1] = gc[1]; dM[2] = gc[2];
-            G[0] = gc[3]; G[1] = gc[4]; G[2] = gc[5];
-            G[3] = gc[4]; G[4] = gc[6]; G[5] = gc[7];
-            G[6] = gc[5]; G[7] = gc[7]; G[8] = gc[8];
+            const ViewDesc& vd = a.views[v];
+            const int64_t g = t - vd.rec_base;
+            float* gc = a.ws.gcam + 9 * t;
+            const float dM[3] = {gc[0], gc[1], gc[2]};
+            const float G[9] = {gc[3], gc[4], gc[5], gc[4], gc[6], gc[7], gc[5], gc[7], gc[8]};
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gc[q] = 0.0f;
+            float R[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) R[q] = vd.R[q];
+            if (vd.grad_means) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    atomicAdd(vd.grad_means + 3 * g + q, R[q] * dM[0] + R[3 + q] * dM[1] + R[6 + q] * dM[2]);
+            }
+            float GR[9];
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+#pragma unroll
+                for (int y = 0; y < 3; ++y) GR[3 * x + y] = G[3 * x] * R[y] + G[3 * x + 1] * R[3 + y] + G[3 * x + 2] * R[6 + y];
+            if (vd.grad_inv_cov) {
+                float Gw[9];
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y) Gw[3 * x + y] = R[x] * GR[y] + R[3 + x] * GR[3 + y] + R[6 + x] * GR[6 + y];
+                float* gp = vd.grad_inv_cov + 6 * g;
+                atomicAdd(gp + 0, Gw[0]);
+                atomicAdd(gp + 1, Gw[1] + Gw[3]);
+                atomicAdd(gp + 2, Gw[2] + Gw[6]);
+                atomicAdd(gp + 3, Gw[4]);
+                atomicAdd(gp + 4, Gw[5] + Gw[7]);
+                atomicAdd(gp + 5, Gw[8]);
+            }
+            if (vd.grad_cam) {
+                gcam_out = vd.grad_cam;
+                float Mw[3], Pw[9];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Mw[q] = __ldg(vd.means + 3 * g + q);
+                const float* p6 = vd.inv_cov + 6 * g;
+                Pw[0] = __ldg(p6 + 0); Pw[1] = __ldg(p6 + 1); Pw[2] = __ldg(p6 + 2);
+                Pw[3] = Pw[1]; Pw[4] = __ldg(p6 + 3); Pw[5] = __ldg(p6 + 4);
+                Pw[6] = Pw[2]; Pw[7] = Pw[5]; Pw[8] = __ldg(p6 + 5);
+                float RP[9];
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y) RP[3 * x + y] = R[3 * x] * Pw[y] + R[3 * x + 1] * Pw[3 + y] + R[3 * x + 2] * Pw[6 + y];
+#pragma unroll
+                for (int x = 0; x < 3; ++x)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y)
+                        p[3 * x + y] = dM[x] * Mw[y] + 2.0f * (G[3 * x] * RP[y] + G[3 * x + 1] * RP[3 + y] + G[3 * x + 2] * RP[6 + y]);
+                p[9] = dM[0];
+                p[10] = dM[1];
+                p[11] = dM[2];
+            }
         }
-        // world mean gradient Rᵀ dM
-        for (int q = 0; q < 3; ++q) gm[q] += R[q] * dM[0] + R[3 + q] * dM[1] + R[6 + q] * dM[2];
-        // world P gradient Rᵀ G R
-        float GR[9];
-        for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) GR[3 * x + y] = G[3 * x] * R[y] + G[3 * x + 1] * R[3 + y] + G[3 * x + 2] * R[6 + y];
-        float Gw[9];
-        for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) Gw[3 * x + y] = R[x] * GR[y] + R[3 + x] * GR[3 + y] + R[6 + x] * GR[6 + y];
-        gw[0] += Gw[0]; gw[1] += Gw[1] + Gw[3]; gw[2] += Gw[2] + Gw[6];
-        gw[3] += Gw[4]; gw[4] += Gw[5] + Gw[7]; gw[5] += Gw[8];
-        if (grad_cam) {
-            // pose: dR = dM Mwᵀ + 2 G (R Pw), dT = dM
-            float RP[9];
-            for (int x = 0; x < 3; ++x)
-                for (int y = 0; y < 3; ++y) RP[3 * x + y] = R[3 * x] * Pw[y] + R[3 * x + 1] * Pw[3 + y] + R[3 * x + 2] * Pw[6 + y];
-            float p[12];
-            for (int x = 0; x < 3; ++x)
-                for (int y = 0; y < 3; ++y)
-                    p[3 * x + y] = dM[x] * Mw[y] + 2.0f * (G[3 * x] * RP[y] + G[3 * x + 1] * RP[3 + y] + G[3 * x + 2] * RP[6 + y]);
-            p[9] = dM[0]; p[10] = dM[1]; p[11] = dM[2];
+        // pose sums: one warp reduction when the warp's records share a view
+        const int v0 = __shfl_sync(0xffffffffu, v, 0);
+        float* out0 = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(gcam_out), 0));
+        const bool uniform = __all_sync(0xffffffffu, v == v0 || v < 0) && v0 >= 0;
+        if (uniform) {
+#pragma unroll
             for (int q = 0; q < 12; ++q) {
                 float x = p[q];
+#pragma unroll
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 p[q] = x;
             }
-            if (lane == 0)
-                for (int q = 0; q < 12; ++q) red[wid][q] = p[q];
-            __syncthreads();
-            if (threadIdx.x < 12) {
-                float s = 0.0f;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-                atomicAdd(grad_cam + 12 * v + threadIdx.x, s);
-            }
-            __syncthreads();
+            if (lane == 0 && out0)
+#pragma unroll
+                for (int q = 0; q < 12; ++q) atomicAdd(out0 + q, p[q]);
+        } else if (gcam_out) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) atomicAdd(gcam_out + q, p[q]);
         }
     }
-    if (!live) return;
-    if (grad_means)
-        for (int q = 0; q < 3; ++q) grad_means[3 * (int64_t)g + q] += gm[q];
-    if (grad_inv_cov)
-        for (int q = 0; q < 6; ++q) grad_inv_cov[6 * (int64_t)g + q] += gw[q];
 }
 
 template <typename Kern>
@@ -362,6 +406,26 @@ static size_t backward_smem_bytes() {
     return (size_t)KM * 16 * TH * 16;
 }
 
+template <typename Kern>
+static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nthreads, smem) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
+// Resident CTAs per SM of the backward tile kernel for capacity KM.
+int backward_blocks_per_sm(int KM) {
+    switch (KM) {
+        case 8: return blocks_per_sm(k_backward<8, 16>, 256, backward_smem_bytes<8, 16>());
+        case 16: return blocks_per_sm(k_backward<16, 16>, 256, backward_smem_bytes<16, 16>());
+        case 20: return blocks_per_sm(k_backward<20, 16>, 256, backward_smem_bytes<20, 16>());
+        case 24: return blocks_per_sm(k_backward<24, 16>, 256, backward_smem_bytes<24, 16>());
+        case 32: return blocks_per_sm(k_backward<32, 8>, 128, backward_smem_bytes<32, 8>());
+        default: return blocks_per_sm(k_backward_generic, 256, 0);
+    }
+}
+
 // Launch the backward tile kernel for register-list capacity KM (0 = generic).
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a) {
     switch (KM) {
@@ -374,10 +438,89 @@ cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Arg
     }
 }
 
-cudaError_t launch_grad_finalize(int N, cudaStream_t s, const Args& a, float* grad_means, float* grad_inv_cov,
-                                 float* grad_cam) {
+// Shared-scene form (every view renders the same N Gaussians): one thread
+// per Gaussian loops over the views, so world gradients are written once
+// without atomics, and the pose sums are reduced per block.
+__global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
+    __shared__ float red[8][12];
+    const int nv = a.hdr->nviews;
+    const int N = a.views[0].N;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int gb = blockIdx.x * blockDim.x; gb < N; gb += gridDim.x * blockDim.x) {
+        const int g = gb + threadIdx.x;
+        const bool live = g < N;
+        float gm[3] = {0.f, 0.f, 0.f}, gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float Mw[3] = {0.f, 0.f, 0.f}, Pw[9];
+        const ViewDesc& v0 = a.views[0];
+        if (live) {
+            for (int q = 0; q < 3; ++q) Mw[q] = __ldg(v0.means + 3 * (int64_t)g + q);
+            const float* p6 = v0.inv_cov + 6 * (int64_t)g;
+            Pw[0] = __ldg(p6 + 0); Pw[1] = __ldg(p6 + 1); Pw[2] = __ldg(p6 + 2);
+            Pw[3] = Pw[1]; Pw[4] = __ldg(p6 + 3); Pw[5] = __ldg(p6 + 4);
+            Pw[6] = Pw[2]; Pw[7] = Pw[5]; Pw[8] = __ldg(p6 + 5);
+        } else {
+            for (int q = 0; q < 9; ++q) Pw[q] = 0.0f;
+        }
+        for (int v = 0; v < nv; ++v) {
+            const ViewDesc& vd = a.views[v];
+            float R[9];
+            for (int q = 0; q < 9; ++q) R[q] = vd.R[q];
+            float dM[3] = {0.f, 0.f, 0.f}, G[9];
+            for (int q = 0; q < 9; ++q) G[q] = 0.0f;
+            if (live) {
+                float* gc = a.ws.gcam + 9 * (vd.rec_base + g);
+                dM[0] = gc[0]; dM[1] = gc[1]; dM[2] = gc[2];
+                G[0] = gc[3]; G[1] = gc[4]; G[2] = gc[5];
+                G[3] = gc[4]; G[4] = gc[6]; G[5] = gc[7];
+                G[6] = gc[5]; G[7] = gc[7]; G[8] = gc[8];
+                for (int q = 0; q < 9; ++q) gc[q] = 0.0f;
+            }
+            for (int q = 0; q < 3; ++q) gm[q] += R[q] * dM[0] + R[3 + q] * dM[1] + R[6 + q] * dM[2];
+            float GR[9];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) GR[3 * x + y] = G[3 * x] * R[y] + G[3 * x + 1] * R[3 + y] + G[3 * x + 2] * R[6 + y];
+            float Gw[9];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) Gw[3 * x + y] = R[x] * GR[y] + R[3 + x] * GR[3 + y] + R[6 + x] * GR[6 + y];
+            gw[0] += Gw[0]; gw[1] += Gw[1] + Gw[3]; gw[2] += Gw[2] + Gw[6];
+            gw[3] += Gw[4]; gw[4] += Gw[5] + Gw[7]; gw[5] += Gw[8];
+            if (vd.grad_cam) {
+                float RP[9];
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y) RP[3 * x + y] = R[3 * x] * Pw[y] + R[3 * x + 1] * Pw[3 + y] + R[3 * x + 2] * Pw[6 + y];
+                float p[12];
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y)
+                        p[3 * x + y] = dM[x] * Mw[y] + 2.0f * (G[3 * x] * RP[y] + G[3 * x + 1] * RP[3 + y] + G[3 * x + 2] * RP[6 + y]);
+                p[9] = dM[0]; p[10] = dM[1]; p[11] = dM[2];
+                for (int q = 0; q < 12; ++q) {
+                    float x = p[q];
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    p[q] = x;
+                }
+                if (lane == 0)
+                    for (int q = 0; q < 12; ++q) red[wid][q] = p[q];
+                __syncthreads();
+                if (threadIdx.x < 12) {
+                    float sum = 0.0f;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+                    atomicAdd(vd.grad_cam + threadIdx.x, sum);
+                }
+                __syncthreads();
+            }
+        }
+        if (!live) continue;
+        if (v0.grad_means)
+            for (int q = 0; q < 3; ++q) v0.grad_means[3 * (int64_t)g + q] += gm[q];
+        if (v0.grad_inv_cov)
+            for (int q = 0; q < 6; ++q) v0.grad_inv_cov[6 * (int64_t)g + q] += gw[q];
+    }
+}
+
+cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a) {
     TraceScope tr("k_grad_finalize", s);
-    k_grad_finalize<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, grad_means, grad_inv_cov, grad_cam);
+    if (shared_scene) k_grad_finalize_shared<<<grid, 256, 0, s>>>(a);
+    else k_grad_finalize<<<grid, 256, 0, s>>>(a);
     return cudaPeekAtLastError();
 }
 

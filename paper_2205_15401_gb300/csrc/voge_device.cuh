@@ -32,19 +32,59 @@ constexpr int kTileW = 16;     // tile width in pixels (one warp covers 16 x 2 p
 constexpr int kSortMax = 2048; // tiles with more candidates are processed unsorted
 constexpr float kLog2e = 1.4426950408889634f;
 
-// Per-view camera as the kernels read it (built on the host from voge_camera).
-struct CamDev {
+// One view as the kernels read it: the camera, the scene this view renders
+// (its own Gaussians, attribute width, list length) and where its outputs go.
+// A render call fills one per view, all pointing at the same scene; a serving
+// tick fills one per admitted request, each with its own scene, so that one
+// launch covers every request.
+struct ViewDesc {
     float R[9];
     float T[3];
     float F, Ox, Oy, invF;
     int32_t H, W, tiles_x, tiles_y;
     int32_t tile_base;  // first global tile id of this view
     int32_t tile_h;     // tile height in pixels
-    int32_t pad0, pad1;
-    int64_t pix_base;   // first global pixel id of this view
-    int64_t pad2;
+    int32_t N, C;       // Gaussians and attribute channels of this view's scene
+    int32_t L;          // list length (<= the register capacity of the launch)
+    int32_t use_thresh, plain, pad0;
+    float tau, Qeta;    // Qeta = 2 ln(1/eta) or +inf
+    float pad1, pad2;
+    int64_t rec_base;   // record of (this view, Gaussian g) is rec_base + g
+    int64_t elem_base;  // first image element of this view in the batch (for per-element kernels)
+    int64_t pix_base;   // first pixel of this view in the batch (generic-path scratch)
+    int64_t pad3;
+    const float* means;
+    const float* inv_cov;
+    const float* attr;
+    float* image;       // this view's first pixel: [H*W][C]
+    float* weights;     // [H*W][L] or null
+    int32_t* index;     // [H*W][L]
+    const int32_t* index_in;
+    const float* grad_image;  // [H*W][C]
+    const float* target;      // [H*W][C] (loss helper)
+    float* loss;              // one float (loss helper)
+    float* grad_means;        // [N][3] or null
+    float* grad_inv_cov;      // [N][6] or null
+    float* grad_attr;         // [N][C] or null
+    float* grad_cam;          // [12] or null
 };
-static_assert(sizeof(CamDev) == 112, "CamDev layout");
+static_assert(sizeof(ViewDesc) % 16 == 0, "ViewDesc layout");
+
+// Per-call (or per-tick) totals and work counters, in device memory next to
+// the view table.  The counters start at zero on every upload.
+constexpr int kMaxClasses = 8;
+struct BatchHdr {
+    int64_t total_records;  // sum over views of N
+    int64_t total_elems;    // sum over views of H*W*C
+    int32_t total_tiles;
+    int32_t nviews;
+    int32_t class_begin[kMaxClasses];  // tile ranges of the list-capacity classes
+    int32_t class_end[kMaxClasses];
+    int32_t counters[2 * kMaxClasses]; // persistent-launch work counters (forward, backward)
+    int32_t shared_scene;   // 1: every view renders the same Gaussians (records rec_base = v * N)
+    int32_t pad[1];
+};
+static_assert(sizeof(BatchHdr) % 16 == 0, "BatchHdr layout");
 
 // Projected record of one (view, Gaussian): 4 x float4 = 64 bytes.
 //   r0 = (uc_hi, uc_lo, vc_hi, vc_lo)   centre, pixel units (u = column + 0.5)
@@ -270,47 +310,67 @@ __device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1
     }
 }
 
-__device__ __forceinline__ int find_view(const CamDev* __restrict__ cams, int B, int tile) {
-    int lo = 0, hi = B - 1;
+// View of a global tile / record / image element (binary searches over the
+// view table's monotone bases).
+__device__ __forceinline__ int view_of_tile(const ViewDesc* __restrict__ vd, int nv, int tile) {
+    int lo = 0, hi = nv - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&cams[mid].tile_base) <= tile) lo = mid;
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&vd[mid].tile_base) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int view_of_record(const ViewDesc* __restrict__ vd, int nv, int64_t r) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&vd[mid].rec_base) <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int view_of_elem(const ViewDesc* __restrict__ vd, int nv, int64_t e) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&vd[mid].elem_base) <= e) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-// Workspace views shared by the launches of one render call.
+// Workspace arrays shared by the launches of one call / tick.
 struct Ws {
-    CamDev* cams;
-    float4* rec;      // [B*N][4]
-    float4* rec2;     // [B*N][2]
-    int4* tbox;       // [B*N]: tile range tx0, tx1, ty0, ty1 (tx0 > tx1: none)
+    float4* rec;      // [records][4]
+    float4* rec2;     // [records][2]
+    int4* tbox;       // [records]: tile range tx0, tx1, ty0, ty1 (tx0 > tx1: none)
     int32_t* tile_cnt;
     int32_t* tile_off;
     int32_t* tile_cur;
     int32_t* tile_gauss;
     int64_t bin_cap;
-    float* gcam;      // [B*N][9] backward accumulators (dM 3, G 6)
-    float* gkey;      // [pixels][L] generic path lists
+    float* gcam;      // [records][9] backward accumulators (dM 3, G 6)
+    float* gkey;      // generic-path per-pixel scratch
     int32_t* gid;
-    int32_t total_tiles;
+    int32_t gen_L;    // list length the generic scratch is laid out for
 };
 
 struct Args {
-    int32_t B, N, C, K, L;  // K: requested, L: list length
-    float tau, Qeta;
-    int32_t use_thresh, plain;
-    const float* means;
-    const float* inv_cov;
-    const float* attr;
-    float* image;
-    float* weights;
-    int32_t* index;
-    const int32_t* index_in;
-    const float* grad_image;
-    float* grad_attr;
+    const ViewDesc* views;
+    BatchHdr* hdr;
     Ws ws;
+    int32_t cls;      // list-capacity class of a tile launch (index into class_begin/end)
 };
+
+// Next tile of a persistent tile launch (dynamic: CTAs take tiles as they
+// free up).  Returns a global tile id or -1 when the class range is done.
+__device__ __forceinline__ int next_tile(const Args& a, int fwd, int* s_slot) {
+    if (threadIdx.x == 0) *s_slot = atomicAdd(&a.hdr->counters[a.cls + (fwd ? 0 : kMaxClasses)], 1);
+    __syncthreads();
+    const int t = a.hdr->class_begin[a.cls] + *s_slot;
+    __syncthreads();
+    return t < a.hdr->class_end[a.cls] ? t : -1;
+}
 
 }  // namespace voge

@@ -51,13 +51,14 @@ struct TileSrc {
 };
 
 template <int NT>
-__device__ __forceinline__ TileSrc tile_source(const Args& a, int t, int tx, int ty, int v, float* s_key,
+__device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd, int t, float* s_key,
                                                int32_t* s_id) {
     TileSrc src;
     src.filter_box = 0;
-    if (a.plain) {
+    const int N = vd.N;
+    if (vd.plain) {
         src.mode = 2;
-        src.count = a.N;
+        src.count = N;
         src.start = 0;
         return src;
     }
@@ -66,16 +67,16 @@ __device__ __forceinline__ TileSrc tile_source(const Args& a, int t, int tx, int
     if ((int64_t)off + cnt > a.ws.bin_cap) {  // binning overflowed: test every Gaussian against its box
         src.mode = 2;
         src.filter_box = 1;
-        src.count = a.N;
+        src.count = N;
         src.start = 0;
         return src;
     }
     src.count = cnt;
     src.start = off;
-    if (a.use_thresh && cnt > 1 && cnt <= kSortMax) {
+    if (vd.use_thresh && cnt > 1 && cnt <= kSortMax) {
         int n2 = 1;
         while (n2 < cnt) n2 <<= 1;
-        const int64_t vb = (int64_t)v * a.N;
+        const int64_t vb = vd.rec_base;
         for (int x = threadIdx.x; x < n2; x += NT) {
             if (x < cnt) {
                 const int32_t g = a.ws.tile_gauss[off + x];
@@ -96,7 +97,7 @@ __device__ __forceinline__ TileSrc tile_source(const Args& a, int t, int tx, int
 }
 
 template <int KM, int TH>
-__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
+__device__ __forceinline__ void render_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     // phase 1 layout: stage[4][NT] float4 | sgid[NT] | skey[kSortMax] | sid[kSortMax] | siv[TH][NT]
@@ -109,21 +110,21 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
     // phase 2 layout: jst[KM][NT] float4 (aliases phase 1)
     float4* jst = smem;
 
-    const CamDev* cams = a.ws.cams;
-    const int t = blockIdx.x;
-    const int v = find_view(cams, a.B, t);
-    const int lt = t - __ldg(&cams[v].tile_base);
-    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int v = view_of_tile(a.views, a.hdr->nviews, t);
+    const ViewDesc& vd = a.views[v];
+    const int lt = t - vd.tile_base;
+    const int tiles_x = vd.tiles_x;
     const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
+    const int H = vd.H, W = vd.W;
     const int tid = threadIdx.x;
     const int j = tx * kTileW + (tid & 15);
     const int i = ty * TH + (tid >> 4);
     const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
-    const int64_t vb = (int64_t)v * a.N;
-    const int K = a.L;  // list length (<= KM)
+    const int64_t pix = (int64_t)i * W + j;  // pixel within the view
+    const int64_t vb = vd.rec_base;
+    const int K = vd.L;  // list length (<= KM)
+    const float Qeta = vd.Qeta;
 
     float key[KM];
     int32_t id[KM];
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
         id[s] = -1;
     }
 
-    const TileSrc src = tile_source<NT>(a, t, tx, ty, v, skey, sid);
+    const TileSrc src = tile_source<NT>(a, vd, t, skey, sid);
     bool active = valid;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
 #pragma unroll
                 for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;
             } else {
-                row_intervals<TH>(r0, r1, r2, r3, a.Qeta, tx, ty, siv + tid, NT);
+                row_intervals<TH>(r0, r1, r2, r3, Qeta, tx, ty, siv + tid, NT);
             }
         } else if (tid < ((nc + 3) & ~3)) {
 #pragma unroll
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
                         break;
                     }
                     const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q], r3 = stage[3 * NT + q];
-                    const float l = candidate_key(r0, r1, r2, r3, px, py, a.Qeta);
+                    const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
                     if (l > 0.0f) {
                         const int32_t g = sgid[q];
                         if (l < key[KM - 1] || (l == key[KM - 1] && g < id[KM - 1])) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
         }
     }
-    const float ntl = -a.tau * kLog2e;
+    const float ntl = -vd.tau * kLog2e;
     float Wt[KM];
     {
         int e = 0;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
     // lists in the shared-memory columns its own lanes used for the j-stream
     // (blocks of 32 float4, one per list slot e) and writes each segment with
     // consecutive lanes on consecutive words.
-    const int L = a.L, C = a.C;
+    const int L = vd.L, C = vd.C;
     const int lane = tid & 31, warp = tid >> 5;
     const int nblk = (L + 3) >> 2;  // blocks of 128 words holding 32 x L entries
     auto stg = [&](int x) -> float* { return reinterpret_cast<float*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127); };
@@ -304,10 +305,10 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
         for (int rw = 0; rw < 2; ++rw) {
             const int irow = ty * TH + 2 * warp + rw;
             if (irow >= H) continue;
-            const int64_t first = __ldg(&cams[v].pix_base) + (int64_t)irow * W + tx * kTileW;
+            const int64_t first = (int64_t)irow * W + tx * kTileW;
             const int cnt = ncols * L;
-            int32_t* di = a.index + first * L;
-            float* dw = a.weights ? a.weights + first * L : nullptr;
+            int32_t* di = vd.index + first * L;
+            float* dw = vd.weights ? vd.weights + first * L : nullptr;
             for (int x = lane; x < cnt; x += 32) {
                 di[x] = *reinterpret_cast<const int32_t*>(stg(rw * 16 * L + x));
                 if (dw) dw[x] = *stg(nblk * 128 + rw * 16 * L + x);
@@ -319,16 +320,16 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
         for (int p = 0; p < 32; ++p) {
             const int irow = ty * TH + 2 * warp + (p >> 4), jcol = tx * kTileW + (p & 15);
             if (irow >= H || jcol >= W) continue;
-            const int64_t pp = __ldg(&cams[v].pix_base) + (int64_t)irow * W + jcol;
+            const int64_t pp = (int64_t)irow * W + jcol;
             for (int c0 = 0; c0 < C; c0 += 32) {
                 const int c = c0 + lane;
                 float acc = 0.0f;
                 for (int k = 0; k < L; ++k) {
                     const int32_t g = *reinterpret_cast<const int32_t*>(stg(p * L + k));
                     if (g < 0) break;
-                    if (c < C) acc = fmaf(*stg(nblk * 128 + p * L + k), __ldg(a.attr + (int64_t)g * C + c), acc);
+                    if (c < C) acc = fmaf(*stg(nblk * 128 + p * L + k), __ldg(vd.attr + (int64_t)g * C + c), acc);
                 }
-                if (c < C) a.image[pp * C + c] = acc;
+                if (c < C) vd.image[pp * C + c] = acc;
             }
         }
     } else if (valid) {
@@ -336,9 +337,19 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
             float acc = 0.0f;
 #pragma unroll
             for (int s = 0; s < KM; ++s)
-                if (s >= KM - K && s - (KM - K) < n) acc = fmaf(Wt[s], __ldg(a.attr + (int64_t)id[s] * C + c), acc);
-            a.image[pix * C + c] = acc;
+                if (s >= KM - K && s - (KM - K) < n) acc = fmaf(Wt[s], __ldg(vd.attr + (int64_t)id[s] * C + c), acc);
+            vd.image[pix * C + c] = acc;
         }
+    }
+}
+
+template <int KM, int TH>
+__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
+    __shared__ int s_slot;
+    for (;;) {
+        const int t = next_tile(a, 1, &s_slot);
+        if (t < 0) return;
+        render_tile<KM, TH>(a, t);
     }
 }
 
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_render(Args a) {
 // Generic path for list lengths above the register lists (L > 32): same tile
 // staging, the per-pixel list kept sorted in the workspace.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_render_generic(Args a) {
+__device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
     constexpr int NT = 256, TH = 16;
     extern __shared__ float4 smem[];
     float4* stage = smem;
@@ -354,26 +365,26 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
     float* skey = reinterpret_cast<float*>(sgid + NT);
     int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
 
-    const CamDev* cams = a.ws.cams;
-    const int t = blockIdx.x;
-    const int v = find_view(cams, a.B, t);
-    const int lt = t - __ldg(&cams[v].tile_base);
-    const int tiles_x = __ldg(&cams[v].tiles_x);
+    const int v = view_of_tile(a.views, a.hdr->nviews, t);
+    const ViewDesc& vd = a.views[v];
+    const int lt = t - vd.tile_base;
+    const int tiles_x = vd.tiles_x;
     const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = __ldg(&cams[v].H), W = __ldg(&cams[v].W);
+    const int H = vd.H, W = vd.W;
     const int tid = threadIdx.x;
     const int j = tx * kTileW + (tid & 15);
     const int i = ty * TH + (tid >> 4);
     const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = __ldg(&cams[v].pix_base) + (int64_t)i * W + j;
-    const int64_t vb = (int64_t)v * a.N;
-    const int L = a.L;
-    float* lk = a.ws.gkey + pix * L;
-    int32_t* li = a.ws.gid + pix * L;
+    const int64_t pix = (int64_t)i * W + j;
+    const int64_t vb = vd.rec_base;
+    const int L = vd.L;
+    const int64_t gpix = vd.pix_base + pix;
+    float* lk = a.ws.gkey + gpix * (int64_t)a.ws.gen_L * 8;
+    int32_t* li = a.ws.gid + gpix * (int64_t)a.ws.gen_L;
     int n = 0;
 
-    const TileSrc src = tile_source<NT>(a, t, tx, ty, v, skey, sid);
+    const TileSrc src = tile_source<NT>(a, vd, t, skey, sid);
     bool active = valid;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
@@ -406,7 +417,7 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
                     active = false;
                     break;
                 }
-                const float l = candidate_key(stage[q], stage[NT + q], stage[2 * NT + q], r3, px, py, a.Qeta);
+                const float l = candidate_key(stage[q], stage[NT + q], stage[2 * NT + q], r3, px, py, vd.Qeta);
                 if (l > 0.0f) {
                     const int32_t g = sgid[q];
                     if (n < L || l < lk[L - 1] || (l == lk[L - 1] && g < li[L - 1])) {
@@ -425,34 +436,45 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
         }
         if (__syncthreads_and(!active)) break;
     }
-    if (!valid) return;
-    // fine pass with both loops over the list in global memory (L1 resident)
-    float* lw = a.weights ? a.weights + pix * L : nullptr;
-    for (int k = 0; k < n; ++k) {
-        float4 r0, r1, r2, r3;
-        load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
-        const Entry ek = entry_px(r0, r1, r2, r3, px, py);
-        float A = 0.0f;
-        for (int jj = 0; jj < n; ++jj) {
-            load_rec(a.ws.rec, vb + li[jj], r0, r1, r2, r3);
-            const Entry ej = entry_px(r0, r1, r2, r3, px, py);
-            const float u = ((ek.hi - ej.hi) + (ek.lo - ej.lo)) * ej.r;
-            const float q = erfc_as28(fabsf(u));
-            const float m = 0.5f * ej.a;
-            const float sm = copysignf(m, u);
-            A = fmaf(-sm, q, A + (m + sm));
+    if (valid) {
+        // fine pass with both loops over the list in global memory (L1 resident)
+        float* lw = vd.weights ? vd.weights + pix * L : nullptr;
+        for (int k = 0; k < n; ++k) {
+            float4 r0, r1, r2, r3;
+            load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
+            const Entry ek = entry_px(r0, r1, r2, r3, px, py);
+            float A = 0.0f;
+            for (int jj = 0; jj < n; ++jj) {
+                load_rec(a.ws.rec, vb + li[jj], r0, r1, r2, r3);
+                const Entry ej = entry_px(r0, r1, r2, r3, px, py);
+                const float u = ((ek.hi - ej.hi) + (ek.lo - ej.lo)) * ej.r;
+                const float q = erfc_as28(fabsf(u));
+                const float m = 0.5f * ej.a;
+                const float sm = copysignf(m, u);
+                A = fmaf(-sm, q, A + (m + sm));
+            }
+            lk[L + k] = ex2_approx(-vd.tau * kLog2e * A) * ek.a;  // W_k
         }
-        lk[k] = ex2_approx(-a.tau * kLog2e * A) * ek.a;  // reuse the key slot for W_k
+        for (int k = 0; k < L; ++k) {
+            const bool real = k < n;
+            vd.index[pix * L + k] = real ? li[k] : -1;
+            if (lw) lw[k] = real ? lk[L + k] : 0.0f;
+        }
+        for (int c = 0; c < vd.C; ++c) {
+            float acc = 0.0f;
+            for (int k = 0; k < n; ++k) acc = fmaf(lk[L + k], __ldg(vd.attr + (int64_t)li[k] * vd.C + c), acc);
+            vd.image[pix * vd.C + c] = acc;
+        }
     }
-    for (int k = 0; k < L; ++k) {
-        const bool real = k < n;
-        a.index[pix * L + k] = real ? li[k] : -1;
-        if (lw) lw[k] = real ? lk[k] : 0.0f;
-    }
-    for (int c = 0; c < a.C; ++c) {
-        float acc = 0.0f;
-        for (int k = 0; k < n; ++k) acc = fmaf(lk[k], __ldg(a.attr + (int64_t)li[k] * a.C + c), acc);
-        a.image[pix * a.C + c] = acc;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_render_generic(Args a) {
+    __shared__ int s_slot;
+    for (;;) {
+        const int t = next_tile(a, 1, &s_slot);
+        if (t < 0) return;
+        render_tile_generic(a, t);
     }
 }
 
@@ -476,7 +498,28 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
     return cudaPeekAtLastError();
 }
 
-// Launch the forward tile kernel for register-list capacity KM (0 = generic).
+template <typename Kern>
+static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nthreads, smem) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
+// Resident CTAs per SM of the forward tile kernel for capacity KM.
+int render_blocks_per_sm(int KM) {
+    switch (KM) {
+        case 8: return blocks_per_sm(k_render<8, 16>, 256, render_smem_bytes(8, 16));
+        case 16: return blocks_per_sm(k_render<16, 16>, 256, render_smem_bytes(16, 16));
+        case 20: return blocks_per_sm(k_render<20, 16>, 256, render_smem_bytes(20, 16));
+        case 24: return blocks_per_sm(k_render<24, 16>, 256, render_smem_bytes(24, 16));
+        case 32: return blocks_per_sm(k_render<32, 8>, 128, render_smem_bytes(32, 8));
+        default: return blocks_per_sm(k_render_generic, 256, render_smem_bytes(0, 16));
+    }
+}
+
+// Launch the forward tile kernel for register-list capacity KM (0 = generic):
+// `nblocks` persistent CTAs that take tiles of class a.cls from the header.
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a) {
     switch (KM) {
         case 8: return launch_tiles(k_render<8, 16>, "k_render<8>", nblocks, 256, render_smem_bytes(8, 16), s, a);

@@ -13,13 +13,13 @@
 
 namespace voge {
 
-__global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams, Args a, int count_tiles) {
-    const int64_t BN = (int64_t)a.B * a.N;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= BN) return;
-    const int v = (int)(t / a.N);
-    const int g = (int)(t - (int64_t)v * a.N);
-    const CamDev& c = cams[v];
+__device__ __forceinline__ void project_one(const Args& a, int v, int64_t t, int count_tiles) {
+    const ViewDesc& c = a.views[v];
+    const int g = (int)(t - __ldg(&c.rec_base));
+    const float* means = c.means;
+    const float* inv_cov = c.inv_cov;
+    const int use_thresh = __ldg(&c.use_thresh);
+    const float Qeta = __ldg(&c.Qeta);
     float R[9], T[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) R[q] = __ldg(&c.R[q]);
@@ -28,12 +28,13 @@ __global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams
     const float F = __ldg(&c.F), Ox = __ldg(&c.Ox), Oy = __ldg(&c.Oy), invF = __ldg(&c.invF);
     const int H = __ldg(&c.H), W = __ldg(&c.W), tiles_x = __ldg(&c.tiles_x), tile_h = __ldg(&c.tile_h);
     const int tile_base = __ldg(&c.tile_base);
+    const int plain = __ldg(&c.plain);
 
-    const float X = __ldg(a.means + 3 * (int64_t)g), Y = __ldg(a.means + 3 * (int64_t)g + 1),
-                Z = __ldg(a.means + 3 * (int64_t)g + 2);
+    const float X = __ldg(means + 3 * (int64_t)g), Y = __ldg(means + 3 * (int64_t)g + 1),
+                Z = __ldg(means + 3 * (int64_t)g + 2);
     float pw[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) pw[q] = __ldg(a.inv_cov + 6 * (int64_t)g + q);
+    for (int q = 0; q < 6; ++q) pw[q] = __ldg(inv_cov + 6 * (int64_t)g + q);
 
     // camera-space mean in double-float
     dfl Mx = df_dot3_add(R[0], X, R[1], Y, R[2], Z, T[0]);
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams
         // |l - Mz| <= sqrt(Qeta Sigma_zz), Sigma_zz = a22 / det P.
         const float detP = fmaf(P[0], a00, fmaf(P[1], a01, P[2] * a02));
         float lmin = -INFINITY;
-        if (a.use_thresh && detP > 0.0f && a22 > 0.0f) {
-            const float h = sqrtf(a.Qeta * a22 / detP);
+        if (use_thresh && detP > 0.0f && a22 > 0.0f) {
+            const float h = sqrtf(Qeta * a22 / detP);
             lmin = Mz.hi - (1.001f * h + 1e-6f * Mz.hi);
         }
         r3 = make_float4(s2 * c22, Mz.hi, Mz.lo, lmin);
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams
         // tile box of the conic qb - Qeta b < 0 (pixel units)
         int j0 = 0, j1 = W - 1, i0 = 0, i1 = H - 1;
         bool empty = false;
-        if (a.use_thresh) {
-            const float Q = a.Qeta;
+        if (use_thresh) {
+            const float Q = Qeta;
             const float h00 = fmaf(-Q, r1.w, r2.z);
             const float h01 = fmaf(-Q, 0.5f * r2.x, 0.5f * r2.w);
             const float h11 = fmaf(-Q, r2.y, r3.x);
@@ -147,17 +148,26 @@ __global__ void __launch_bounds__(256) k_project(const CamDev* __restrict__ cams
     a.ws.rec2[2 * t + 0] = s0;
     a.ws.rec2[2 * t + 1] = s1;
     a.ws.tbox[t] = tb;
-    if (count_tiles) {
+    if (count_tiles && !plain) {
         for (int ty = tb.z; ty <= tb.w; ++ty)
             for (int tx = tb.x; tx <= tb.y; ++tx) atomicAdd(&a.ws.tile_cnt[tile_base + ty * tiles_x + tx], 1);
     }
 }
 
+__global__ void __launch_bounds__(256) k_project(Args a, int count_tiles) {
+    const int nv = a.hdr->nviews;
+    const int64_t total = a.hdr->total_records;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        project_one(a, view_of_record(a.views, nv, t), t, count_tiles);
+    }
+}
+
 // Exclusive scan of the per-tile counts (one CTA of 1024 threads; each thread
 // owns a contiguous run).  Also seeds the scatter cursors.
-__global__ void __launch_bounds__(1024) k_scan_tiles(Ws ws) {
+__global__ void __launch_bounds__(1024) k_scan_tiles(Args a) {
     __shared__ int32_t warp_sums[32];
-    const int n = ws.total_tiles;
+    const Ws& ws = a.ws;
+    const int n = a.hdr->total_tiles;
     const int tid = threadIdx.x;
     const int per = (n + 1023) / 1024;
     const int beg = min(n, tid * per), end = min(n, beg + per);
@@ -191,39 +201,42 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Ws ws) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(const CamDev* __restrict__ cams, Args a) {
-    const int64_t BN = (int64_t)a.B * a.N;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= BN) return;
-    const int4 tb = a.ws.tbox[t];
-    if (tb.x > tb.y) return;
-    const int v = (int)(t / a.N);
-    const int g = (int)(t - (int64_t)v * a.N);
-    const int tiles_x = __ldg(&cams[v].tiles_x), tile_base = __ldg(&cams[v].tile_base);
-    for (int ty = tb.z; ty <= tb.w; ++ty)
-        for (int tx = tb.x; tx <= tb.y; ++tx) {
-            int pos = atomicAdd(&a.ws.tile_cur[tile_base + ty * tiles_x + tx], 1);
-            if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
-        }
+__global__ void __launch_bounds__(256) k_scatter(Args a) {
+    const int nv = a.hdr->nviews;
+    const int64_t total = a.hdr->total_records;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int4 tb = a.ws.tbox[t];
+        if (tb.x > tb.y) continue;
+        const int v = view_of_record(a.views, nv, t);
+        if (__ldg(&a.views[v].plain)) continue;
+        const int g = (int)(t - __ldg(&a.views[v].rec_base));
+        const int tiles_x = __ldg(&a.views[v].tiles_x), tile_base = __ldg(&a.views[v].tile_base);
+        for (int ty = tb.z; ty <= tb.w; ++ty)
+            for (int tx = tb.x; tx <= tb.y; ++tx) {
+                const int pos = atomicAdd(&a.ws.tile_cur[tile_base + ty * tiles_x + tx], 1);
+                if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
+            }
+    }
 }
 
-// Upload-free part of the projection: k_project, then (with count_tiles) the
-// tile scan and scatter.
-cudaError_t launch_project(int64_t BN, int count_tiles, cudaStream_t s, const Args& a) {
-    if (BN > 0) {
+// Projection of every (view, Gaussian) record, then (with count_tiles) the
+// tile scan and scatter.  Grid-stride kernels: `grid` blocks of 256 threads
+// cover any number of records read from the batch header.
+cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args& a) {
+    {
         TraceScope tr("k_project", s);
-        k_project<<<(unsigned)((BN + 255) / 256), 256, 0, s>>>(a.ws.cams, a, count_tiles);
+        k_project<<<grid, 256, 0, s>>>(a, count_tiles);
         cudaError_t e = cudaPeekAtLastError();
         if (e != cudaSuccess) return e;
     }
     if (count_tiles) {
         {
             TraceScope tr("k_scan_tiles", s);
-            k_scan_tiles<<<1, 1024, 0, s>>>(a.ws);
+            k_scan_tiles<<<1, 1024, 0, s>>>(a);
         }
-        if (BN > 0) {
+        {
             TraceScope tr("k_scatter", s);
-            k_scatter<<<(unsigned)((BN + 255) / 256), 256, 0, s>>>(a.ws.cams, a);
+            k_scatter<<<grid, 256, 0, s>>>(a);
         }
         return cudaPeekAtLastError();
     }

@@ -304,3 +304,142 @@ class VoGERender(torch.autograd.Function):
 def render(means, inv_cov, attr, renderer, cam_grad=None):
     """Differentiable render; returns (image [P,C], weights [P,L], index [P,L])."""
     return VoGERender.apply(means, inv_cov, attr, renderer, cam_grad)
+
+
+# --------------------------------------------------------------- serving ---
+class voge_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("batching", ctypes.c_int32), ("inflight_ticks", ctypes.c_int32),
+                ("max_tick_gaussians", ctypes.c_int64), ("max_tick_pixels", ctypes.c_int64),
+                ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class voge_request(ctypes.Structure):
+    _fields_ = [("cam", voge_camera), ("scene", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("tau", ctypes.c_float), ("thresh", ctypes.c_float),
+                ("means", ctypes.c_void_p), ("inv_cov", ctypes.c_void_p), ("attr", ctypes.c_void_p),
+                ("target", ctypes.c_void_p), ("image", ctypes.c_void_p), ("grad_means", ctypes.c_void_p),
+                ("grad_inv_cov", ctypes.c_void_p), ("grad_attr", ctypes.c_void_p), ("grad_cam", ctypes.c_void_p),
+                ("loss", ctypes.c_void_p)]
+
+
+class voge_request_timing(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double), ("start_us", ctypes.c_double),
+                ("done_us", ctypes.c_double), ("tick", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class voge_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("ticks", ctypes.c_int64), ("requests_in_ticks", ctypes.c_int64),
+                ("graphs_captured", ctypes.c_int64), ("queued", ctypes.c_int64), ("resident", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_bound", False):
+        P, vp = ctypes.POINTER, ctypes.c_void_p
+        L.voge_server_create.argtypes = [P(voge_server_config), P(vp)]
+        L.voge_server_create.restype = ctypes.c_int
+        L.voge_server_submit.argtypes = [vp, P(voge_request), P(ctypes.c_uint64)]
+        L.voge_server_submit.restype = ctypes.c_int
+        L.voge_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, P(voge_request_timing)]
+        L.voge_server_wait.restype = ctypes.c_int
+        L.voge_server_get_stats.argtypes = [vp, P(voge_server_stats)]
+        L.voge_server_get_stats.restype = ctypes.c_int
+        L.voge_server_add_scene.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, P(ctypes.c_int32)]
+        L.voge_server_add_scene.restype = ctypes.c_int
+        L.voge_server_remove_scene.argtypes = [vp, ctypes.c_int32]
+        L.voge_server_remove_scene.restype = ctypes.c_int
+        L.voge_server_pause.argtypes = [vp, ctypes.c_int32]
+        L.voge_server_pause.restype = ctypes.c_int
+        L.voge_server_destroy.argtypes = [vp]
+        L.voge_server_destroy.restype = ctypes.c_int
+        L._server_bound = True
+    return L
+
+
+def _host_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"] and t.dtype == np.float32
+        return ctypes.c_void_p(t.ctypes.data)
+    assert isinstance(t, torch.Tensor) and not t.is_cuda and t.is_contiguous() and t.dtype == torch.float32
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Server:
+    """voge_server_* through ctypes.  Host arrays of a request (numpy float32 or
+    CPU torch tensors, preferably pinned) are kept referenced until its wait."""
+
+    def __init__(self, mem_budget_bytes=8 << 30, max_slots=64, use_graphs=True, batching=True, inflight_ticks=2,
+                 max_tick_gaussians=0, max_tick_pixels=0, max_queue=0, device=None):
+        L = _server_lib()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        cfg = voge_server_config(dev, int(max_slots), int(max_queue), int(bool(use_graphs)), int(bool(batching)),
+                                 int(inflight_ticks), int(max_tick_gaussians), int(max_tick_pixels),
+                                 int(mem_budget_bytes))
+        h = ctypes.c_void_p()
+        _check(L.voge_server_create(ctypes.byref(cfg), ctypes.byref(h)), "voge_server_create")
+        self.h = h
+        self.keep = {}
+
+    def add_scene(self, means, inv_cov, attr):
+        m, p, a = (np.ascontiguousarray(x, dtype=np.float32) for x in (means, inv_cov, attr))
+        sid = ctypes.c_int32()
+        _check(_server_lib().voge_server_add_scene(self.h, m.shape[0], a.shape[1], _host_ptr(m), _host_ptr(p),
+                                                     _host_ptr(a), ctypes.byref(sid)), "voge_server_add_scene")
+        return int(sid.value)
+
+    def remove_scene(self, sid):
+        return int(_server_lib().voge_server_remove_scene(self.h, int(sid)))
+
+    def submit(self, cam, target, K, tau=1.0, thresh=0.01, scene=-1, means=None, inv_cov=None, attr=None,
+               outputs=None):
+        """outputs: dict of host buffers image / grad_means / grad_inv_cov / grad_attr / grad_cam / loss."""
+        outputs = outputs or {}
+        req = voge_request()
+        req.cam = make_cameras([cam])[0]
+        req.scene = int(scene)
+        if scene < 0:
+            req.N, req.C = int(means.shape[0]), int(attr.shape[1])
+        req.K, req.tau, req.thresh = int(K), float(tau), float(thresh)
+        req.means, req.inv_cov, req.attr = _host_ptr(means), _host_ptr(inv_cov), _host_ptr(attr)
+        req.target = _host_ptr(target)
+        for k in ("image", "grad_means", "grad_inv_cov", "grad_attr", "grad_cam", "loss"):
+            setattr(req, k, _host_ptr(outputs.get(k)))
+        t = ctypes.c_uint64()
+        rc = _server_lib().voge_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if rc != VOGE_OK:
+            return rc, None
+        self.keep[int(t.value)] = (target, means, inv_cov, attr, outputs)
+        return rc, int(t.value)
+
+    def wait(self, ticket, timeout_ms=-1):
+        tm = voge_request_timing()
+        rc = _server_lib().voge_server_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(tm))
+        if rc != -5:  # VOGE_ERR_TIMEOUT keeps the ticket alive
+            self.keep.pop(ticket, None)
+        return rc, {"submit_us": tm.submit_us, "admit_us": tm.admit_us, "start_us": tm.start_us,
+                    "done_us": tm.done_us, "tick": tm.tick, "status": tm.status}
+
+    def pause(self, paused=True):
+        _check(_server_lib().voge_server_pause(self.h, int(bool(paused))), "voge_server_pause")
+
+    def stats(self):
+        st = voge_server_stats()
+        _check(_server_lib().voge_server_get_stats(self.h, ctypes.byref(st)), "voge_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in voge_server_stats._fields_ if k != "pad"}
+
+    def close(self):
+        if self.h:
+            _server_lib().voge_server_destroy(self.h)
+            self.h = None
+            self.keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
