@@ -271,6 +271,19 @@ def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
 
 
 # --------------------------------------------------------------- GPU path ---
+def reduce_over_ranks(ms, pixels, world, device):
+    """Whole-job timing: the slowest rank's time and the pixels of all ranks."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pixels)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_15401_gb300", "csrc")
@@ -378,13 +391,8 @@ def main():
     trace = voge.voge_trace_read()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t_max = torch.tensor([ms], device=dev, dtype=torch.float64)
-    pix_all = torch.tensor([P * args.steps], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(pix_all, op=dist.ReduceOp.SUM)
-    ms_max = float(t_max.item())
-    value = float(pix_all.item()) / (ms_max / 1e3) / 1e6
+    ms_max, pix_all = reduce_over_ranks(ms, P * args.steps, world, dev)
+    value = pix_all / (ms_max / 1e3) / 1e6
     launches = sum(n for n, _ in trace.values())
 
     # ------------------------------------------------ roofline of the top kernel
@@ -445,13 +453,11 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
-        t_e2e = torch.tensor([time.perf_counter() - t0], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-        e2e = {"value": float(pix_all.item()) / float(t_e2e.item()) / 1e6, "unit": UNIT,
+        t_e2e, _ = reduce_over_ranks(time.perf_counter() - t0, 0, world, dev)
+        e2e = {"value": pix_all / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (n_par + target.numel())),
                "d2h_bytes_per_step": int(4 * (n_par + g_cam.numel() + 1)),
-               "ms_per_step": 1e3 * float(t_e2e.item()) / args.steps}
+               "ms_per_step": 1e3 * t_e2e / args.steps}
 
     # ------------------------------------------------ plain comparator
     plain = None

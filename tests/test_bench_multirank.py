@@ -1,0 +1,48 @@
+"""bench.py's N > 1 path on CPU: gloo ranks agree on the slowest time and the summed pixels."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    ms, px = bench.reduce_over_ranks(10.0 + 5.0 * rank, 1000 * (rank + 1), world, torch.device("cpu"))
+    out[rank] = (ms, px)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_time_and_pixels():
+    world = 2
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        assert out[r] == (15.0, 3000.0)  # max of 10/15 ms, sum of 1000/2000 pixels
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup, gpus, seed = 1, 0, 2, 0
+
+    assert bench.run_reference(A()) is None  # returns at once, prints nothing
