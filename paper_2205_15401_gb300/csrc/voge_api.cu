@@ -113,7 +113,7 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.tile_off = o; o = align256(o + 4 * (size_t)(tiles + 1));
     l.tile_cur = o; o = align256(o + 4 * (size_t)(tiles + 1));
     l.tile_gauss = o; o = align256(o + 4 * (size_t)l.bin_cap);
-    l.gcam = o; o = align256(o + 36 * (size_t)BN);
+    l.gcam = o; o = align256(o + 4 * kGcamStride * (size_t)BN);
     if (l.KM == 0 && l.L > 0) {
         l.gkey = o; o = align256(o + 32 * (size_t)pixels * l.L);  // 8 floats per entry
         l.gid = o; o = align256(o + 4 * (size_t)pixels * l.L);
@@ -386,7 +386,7 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
     const int project = (p->flags & VOGE_FLAG_REUSE_PROJECTION) ? 0 : 1;
     int rc = upload_and_project(cams, p, l, a, b, project, 0, s);
     if (rc != VOGE_OK) return rc;
-    if (cudaMemsetAsync(a.ws.gcam, 0, 36 * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
+    if (cudaMemsetAsync(a.ws.gcam, 0, 4 * kGcamStride * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
     if (l.total_tiles > 0 && launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
     if ((grad_means || grad_inv_cov || grad_cam) &&

@@ -23,12 +23,9 @@ constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
 // Camera-space gradient of one (pixel, kept Gaussian) pair: out[0..2] = dM,
 // out[3..8] = G (xx, xy, xz, yy, yz, zz) with entries of P treated as independent.
-__device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, float px, float py, float invF, float dqt,
-                                                float dl, float db, float out[9]) {
-    float4 r0, r1, r2, r3;
-    load_rec(a.ws.rec, o, r0, r1, r2, r3);
+__device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const Trace& t, const float4& r3, float px,
+                                                float py, float invF, float dqt, float dl, float db, float out[9]) {
     const float4 s0 = __ldg(a.ws.rec2 + 2 * o), s1 = __ldg(a.ws.rec2 + 2 * o + 1);
-    const Trace t = trace_px(r0, r1, r2, r3, px, py);
     const float ib = 1.0f / t.b;
     const float Mz = r3.y;
     const float dlt = -Mz * t.num * ib;  // l - Mz
@@ -80,32 +77,49 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     const float* attr = vd.attr;
     float* grad_attr = vd.grad_attr;
 
+    // index lists: each warp reads its two 16-pixel row segments (contiguous
+    // [16][L] blocks) with consecutive lanes on consecutive words, through its
+    // own shared-memory columns
+    const int lane = tid & 31, warp = tid >> 5;
+    auto stg = [&](int x) -> int32_t* {
+        return reinterpret_cast<int32_t*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127);
+    };
+    {
+        const int ncols = min(kTileW, W - tx * kTileW);
+#pragma unroll
+        for (int rw = 0; rw < 2; ++rw) {
+            const int irow = ty * TH + 2 * warp + rw;
+            const int cnt = irow < H ? ncols * L : 0;
+            const int32_t* src = vd.index_in + ((int64_t)irow * W + tx * kTileW) * L;
+            for (int x = lane; x < 16 * L; x += 32) *stg(rw * 16 * L + x) = x < cnt ? __ldg(src + x) : -1;
+        }
+    }
+    __syncwarp();
     int32_t id[KM];
+#pragma unroll
+    for (int s = 0; s < KM; ++s) id[s] = (s >= KM - K) ? *stg(lane * L + (s - (KM - K))) : -1;
+    __syncwarp();
     float hi[KM], lo[KM], dA[KM], dl[KM];
-    if (!valid) return;  // no block-wide barriers inside a tile
     int n = 0;
-    bool open = true;
+    bool open = valid;  // lanes outside the image keep no entries but stay for the warp-wide steps
 #pragma unroll
     for (int s = 0; s < KM; ++s) {
-        id[s] = -1;
         hi[s] = 0.0f;
         lo[s] = 0.0f;
         dA[s] = 0.0f;
         dl[s] = 0.0f;
-        if (s >= KM - K && open) {
-            const int32_t g = __ldg(vd.index_in + pix * L + (s - (KM - K)));
-            if (g >= 0 && g < N) {
-                float4 r0, r1, r2, r3;
-                load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
-                const Entry e = entry_px(r0, r1, r2, r3, px, py);
-                hi[s] = e.hi;
-                lo[s] = e.lo;
-                id[s] = g;
-                jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
-                ++n;
-            } else {
-                open = false;
-            }
+        const int32_t g = id[s];
+        if (s >= KM - K && open && g >= 0 && g < N) {
+            float4 r0, r1, r2, r3;
+            load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+            const Entry e = entry_px(r0, r1, r2, r3, px, py);
+            hi[s] = e.hi;
+            lo[s] = e.lo;
+            jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
+            ++n;
+        } else {
+            if (s >= KM - K) open = false;
+            id[s] = -1;
         }
     }
     // loop 1: A_k
@@ -130,8 +144,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
             if (id[s] >= 0) {
-                const float am = jst[e * NT + tid].w;
-                const float Wk = ex2_approx(ntl * A[s]) * (2.0f * am);
+                const float Wk = ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
                 const float* ck = attr + (int64_t)id[s] * C;
                 float G = 0.0f;
                 for (int c = 0; c < C; ++c) {
@@ -144,6 +157,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
             }
         }
     }
+    if (n == 0) return;  // no warp-wide steps below
     // loop 2: adjoint of the pair terms
     for (int e = 0; e < n; ++e) {
         const float4 J = jst[e * NT + tid];
@@ -175,14 +189,17 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
                 float4 r0, r1, r2, r3;
                 const int64_t o = vb + id[s];
                 load_rec(a.ws.rec, o, r0, r1, r2, r3);
-                const Entry en = entry_px(r0, r1, r2, r3, px, py);
-                const float dqt = fmaf(dA[s], inv2tau, -0.25f * en.a * J.x);
-                const float db = J.z / (4.0f * en.r);
+                const Trace tr = trace_px(r0, r1, r2, r3, px, py);
+                const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
+                const float er = sqrtf(0.5f * tr.b);
+                const float dqt = fmaf(dA[s], inv2tau, -0.25f * ea * J.x);
+                const float db = J.z / (4.0f * er);
                 float gv[9];
-                chain_to_camera(a, o, px, py, invF, dqt, dl[s] + J.y, db, gv);
-                float* gc = a.ws.gcam + 9 * o;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) atomicAdd(gc + q, gv[q]);
+                chain_to_camera(a, o, tr, r3, px, py, invF, dqt, dl[s] + J.y, db, gv);
+                float* gc = a.ws.gcam + kGcamStride * o;
+                red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
+                red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
+                red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
                 ++e;
             }
         }
@@ -276,9 +293,14 @@ __device__ __forceinline__ void backward_tile_generic(const Args& a, int t) {
         const float dqt = fmaf(sk[4], inv2tau, -0.5f * sk[3] * sk[6]);  // a/4 = m/2
         const float db = sk[7] / (4.0f * sk[2]);
         float gv[9];
-        chain_to_camera(a, vb + li[k], px, py, invF, dqt, sk[5], db, gv);
-        float* gc = a.ws.gcam + 9 * (vb + li[k]);
-        for (int q = 0; q < 9; ++q) atomicAdd(gc + q, gv[q]);
+        float4 r0, r1, r2, r3;
+        load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
+        const Trace tr = trace_px(r0, r1, r2, r3, px, py);
+        chain_to_camera(a, vb + li[k], tr, r3, px, py, invF, dqt, sk[5], db, gv);
+        float* gc = a.ws.gcam + kGcamStride * (vb + li[k]);
+        red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
+        red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
+        red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -311,7 +333,7 @@ __global__ void __launch_bounds__(256) k_grad_finalize(Args a) {
         if (live) {
             const ViewDesc& vd = a.views[v];
             const int64_t g = t - vd.rec_base;
-            float* gc = a.ws.gcam + 9 * t;
+            float* gc = a.ws.gcam + kGcamStride * t;
             const float dM[3] = {gc[0], gc[1], gc[2]};
             const float G[9] = {gc[3], gc[4], gc[5], gc[4], gc[6], gc[7], gc[5], gc[7], gc[8]};
 #pragma unroll
@@ -468,7 +490,7 @@ __global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
             float dM[3] = {0.f, 0.f, 0.f}, G[9];
             for (int q = 0; q < 9; ++q) G[q] = 0.0f;
             if (live) {
-                float* gc = a.ws.gcam + 9 * (vd.rec_base + g);
+                float* gc = a.ws.gcam + kGcamStride * (vd.rec_base + g);
                 dM[0] = gc[0]; dM[1] = gc[1]; dM[2] = gc[2];
                 G[0] = gc[3]; G[1] = gc[4]; G[2] = gc[5];
                 G[3] = gc[4]; G[4] = gc[6]; G[5] = gc[7];

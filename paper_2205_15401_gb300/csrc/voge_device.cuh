@@ -310,6 +310,17 @@ __device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1
     }
 }
 
+// Camera-space gradient sums per record: 12 floats = three 16-byte groups
+// (dM0 dM1 dM2 G0 | G1 G2 G3 G4 | G5 0 0 0), G = (xx, xy, xz, yy, yz, zz).
+constexpr int kGcamStride = 12;
+
+// Vector reduction into global memory (PTX red.global.add.v4.f32, sm_90+):
+// one operation adds four consecutive floats; the address is 16-byte aligned.
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 // View of a global tile / record / image element (binary searches over the
 // view table's monotone bases).
 __device__ __forceinline__ int view_of_tile(const ViewDesc* __restrict__ vd, int nv, int tile) {
@@ -350,7 +361,7 @@ struct Ws {
     int32_t* tile_cur;
     int32_t* tile_gauss;
     int64_t bin_cap;
-    float* gcam;      // [records][9] backward accumulators (dM 3, G 6)
+    float* gcam;      // [records][12] backward accumulators: dM (3), G (6), zero padding (3)
     float* gkey;      // generic-path per-pixel scratch
     int32_t* gid;
     int32_t gen_L;    // list length the generic scratch is laid out for

@@ -564,7 +564,7 @@ int voge_server_create(const voge_server_config* cfg, voge_server** out) {
     S->ws_off = o; o += up256(4 * (size_t)(S->max_tiles + 1));
     S->ws_cur = o; o += up256(4 * (size_t)(S->max_tiles + 1));
     S->ws_gauss = o; o += up256(4 * (size_t)S->bin_cap);
-    S->ws_gcam = o; o += up256(36 * (size_t)S->max_records);
+    S->ws_gcam = o; o += up256(4 * kGcamStride * (size_t)S->max_records);
     const size_t tick_bytes = o;
     const size_t total = (size_t)S->cfg.inflight_ticks * tick_bytes;
     if (total >= cfg->mem_budget_bytes) {
@@ -603,7 +603,7 @@ int voge_server_create(const voge_server_config* cfg, voge_server** out) {
         a.ws.gkey = nullptr;  // lists longer than 32 are not served
         a.ws.gid = nullptr;
         a.ws.gen_L = 0;
-        ok = ok && cudaMemset(a.ws.gcam, 0, 36 * (size_t)S->max_records) == cudaSuccess;  // finalize keeps it zeroed
+        ok = ok && cudaMemset(a.ws.gcam, 0, 4 * kGcamStride * (size_t)S->max_records) == cudaSuccess;  // finalize keeps it zeroed
     }
     if (!ok) {
         voge_server_destroy(S);
