@@ -107,6 +107,8 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
     int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
     uint16_t* siv = reinterpret_cast<uint16_t*>(sid + kSortMax);
     uint32_t* smask = reinterpret_cast<uint32_t*>(siv + TH * NT);  // [NT/32][NT] per-lane hit masks
+    float* slk = reinterpret_cast<float*>(smask + (NT / 32) * NT);  // [KM][NT] per-lane kept depths
+    int32_t* sli = reinterpret_cast<int32_t*>(slk + KM * NT);      // [KM][NT] per-lane kept indices
     // phase 2 layout: jst[KM][NT] float4 (aliases phase 1)
     float4* jst = smem;
 
@@ -126,13 +128,13 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
     const int K = vd.L;  // list length (<= KM)
     const float Qeta = vd.Qeta;
 
-    float key[KM];
-    int32_t id[KM];
-#pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        key[s] = (s < KM - K) ? -INFINITY : INFINITY;
-        id[s] = -1;
-    }
+    // The kept list of this pixel lives in its own shared-memory column: new
+    // candidates are appended while it fills; once it holds K entries a
+    // nearer candidate replaces the farthest one (kmax, gmax at slot smax).
+    // It is sorted once at the end.
+    int n = 0, smax = 0;
+    float kmax = INFINITY;
+    int32_t gmax = INT32_MAX;
 
     const TileSrc src = tile_source<NT>(a, vd, t, skey, sid);
     bool active = valid;
@@ -201,7 +203,7 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 while (m) {
                     const int q = w * 32 + __ffs(m) - 1;
                     m &= m - 1;
-                    if (src.mode == 1 && lmin[4 * q] > key[KM - 1]) {
+                    if (src.mode == 1 && lmin[4 * q] > kmax) {
                         active = false;  // sorted by lower bound: nothing later can enter
                         m = 0;
                         break;
@@ -210,12 +212,27 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                     const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
                     if (l > 0.0f) {
                         const int32_t g = sgid[q];
-                        if (l < key[KM - 1] || (l == key[KM - 1] && g < id[KM - 1])) {
-                            if (l > key[KM - 2] || (l == key[KM - 2] && g > id[KM - 2])) {
-                                key[KM - 1] = l;  // lands last
-                                id[KM - 1] = g;
-                            } else {
-                                topk_insert<KM>(key, id, l, g);
+                        int slot = -1;
+                        if (n < K) {
+                            slot = n++;
+                        } else if (l < kmax || (l == kmax && g < gmax)) {
+                            slot = smax;
+                        }
+                        if (slot >= 0) {
+                            slk[slot * NT + tid] = l;
+                            sli[slot * NT + tid] = g;
+                            if (n == K) {  // full: find the farthest entry, the bar for later candidates
+                                kmax = -INFINITY;
+                                gmax = -1;
+                                for (int s2 = 0; s2 < K; ++s2) {
+                                    const float x = slk[s2 * NT + tid];
+                                    const int32_t y = sli[s2 * NT + tid];
+                                    if (x > kmax || (x == kmax && y > gmax)) {
+                                        kmax = x;
+                                        gmax = y;
+                                        smax = s2;
+                                    }
+                                }
                             }
                         }
                     }
@@ -226,18 +243,38 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             if (active && src.mode == 1 && nc == NT && base + NT < src.count) {
                 // the first candidate of the next chunk bounds everything after it
                 const float nxt = skey[base + NT];
-                if (nxt > key[KM - 1]) active = false;
+                if (nxt > kmax) active = false;
             }
         }
         if (__syncthreads_and(!active)) break;
+    }
+    // sort the kept list by (l, index): candidates arrive nearly in depth
+    // order, so this insertion sort does little work
+    for (int i = 1; i < n; ++i) {
+        const float x = slk[i * NT + tid];
+        const int32_t y = sli[i * NT + tid];
+        int j = i - 1;
+        while (j >= 0) {
+            const float xj = slk[j * NT + tid];
+            const int32_t yj = sli[j * NT + tid];
+            if (!(xj > x || (xj == x && yj > y))) break;
+            slk[(j + 1) * NT + tid] = xj;
+            sli[(j + 1) * NT + tid] = yj;
+            --j;
+        }
+        slk[(j + 1) * NT + tid] = x;
+        sli[(j + 1) * NT + tid] = y;
+    }
+    int32_t id[KM];
+#pragma unroll
+    for (int s = 0; s < KM; ++s) {
+        const int k = s - (KM - K);
+        id[s] = (k >= 0 && k < n) ? sli[k * NT + tid] : -1;
     }
     __syncthreads();  // staging area becomes the j-stream
 
     // ---------------- fine pass ----------------
     // kept entries occupy slots [KM - K, KM - K + n) in ascending (l, index)
-    int n = 0;
-#pragma unroll
-    for (int s = 0; s < KM; ++s) n += (valid && s >= KM - K && key[s] < INFINITY) ? 1 : 0;
     float hi[KM], lo[KM], A[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s) {
@@ -481,7 +518,7 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
 size_t render_smem_bytes(int KM, int TH) {
     const int NT = 16 * TH;
     const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)kSortMax * 8 + (size_t)NT * TH * 2 +
-                          (size_t)NT * (NT / 32) * 4;
+                          (size_t)NT * (NT / 32) * 4 + (size_t)KM * NT * 8;
     const size_t phase2 = (size_t)KM * NT * 16;
     return phase1 > phase2 ? phase1 : phase2;
 }
