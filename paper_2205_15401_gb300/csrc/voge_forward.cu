@@ -18,30 +18,6 @@
 
 namespace voge {
 
-// Bitonic sort of (key, id) pairs in shared memory, ascending by key.
-template <int NT>
-__device__ void bitonic_sort(float* key, int32_t* id, int n_pow2) {
-    for (int k = 2; k <= n_pow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int x = threadIdx.x; x < n_pow2; x += NT) {
-                const int y = x ^ j;
-                if (y > x) {
-                    const bool up = (x & k) == 0;
-                    const float kx = key[x], ky = key[y];
-                    if ((kx > ky) == up) {
-                        key[x] = ky;
-                        key[y] = kx;
-                        const int32_t t = id[x];
-                        id[x] = id[y];
-                        id[y] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // Candidate source of one tile.
 struct TileSrc {
     int mode;          // 0 = binned list in global, 1 = sorted list in smem, 2 = every Gaussian (plain/overflow)
@@ -50,9 +26,11 @@ struct TileSrc {
     int start;
 };
 
+// Candidate source of a tile.  mode 1: the binned list, sorted by depth lower
+// bound (early exit allowed); mode 0: the binned list unsorted; mode 2: every
+// Gaussian of the view (plain, or the tile's list overflowed the bins).
 template <int NT>
-__device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd, int t, float* s_key,
-                                               int32_t* s_id) {
+__device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd, int t) {
     TileSrc src;
     src.filter_box = 0;
     const int N = vd.N;
@@ -73,26 +51,7 @@ __device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd
     }
     src.count = cnt;
     src.start = off;
-    if (vd.use_thresh && cnt > 1 && cnt <= kSortMax) {
-        int n2 = 1;
-        while (n2 < cnt) n2 <<= 1;
-        const int64_t vb = vd.rec_base;
-        for (int x = threadIdx.x; x < n2; x += NT) {
-            if (x < cnt) {
-                const int32_t g = a.ws.tile_gauss[off + x];
-                s_key[x] = __ldg(&a.ws.rec[4 * (vb + g) + 3].w);
-                s_id[x] = g;
-            } else {
-                s_key[x] = INFINITY;
-                s_id[x] = -1;
-            }
-        }
-        __syncthreads();
-        bitonic_sort<NT>(s_key, s_id, n2);
-        src.mode = 1;
-    } else {
-        src.mode = 0;
-    }
+    src.mode = (vd.use_thresh && cnt > 1 && cnt <= kSortMax) ? 1 : 0;
     return src;
 }
 
@@ -100,12 +59,10 @@ template <int KM, int TH>
 __device__ __forceinline__ void render_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
-    // phase 1 layout: stage[4][NT] float4 | sgid[NT] | skey[kSortMax] | sid[kSortMax] | siv[TH][NT]
+    // phase 1 layout: stage[4][NT] float4 | sgid[NT] | siv[TH][NT] | smask[NT/32][NT] | slk, sli [KM][NT]
     float4* stage = smem;
     int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
-    float* skey = reinterpret_cast<float*>(sgid + NT);
-    int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
-    uint16_t* siv = reinterpret_cast<uint16_t*>(sid + kSortMax);
+    uint16_t* siv = reinterpret_cast<uint16_t*>(sgid + NT);
     uint32_t* smask = reinterpret_cast<uint32_t*>(siv + TH * NT);  // [NT/32][NT] per-lane hit masks
     float* slk = reinterpret_cast<float*>(smask + (NT / 32) * NT);  // [KM][NT] per-lane kept depths
     int32_t* sli = reinterpret_cast<int32_t*>(slk + KM * NT);      // [KM][NT] per-lane kept indices
@@ -136,14 +93,13 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
     float kmax = INFINITY;
     int32_t gmax = INT32_MAX;
 
-    const TileSrc src = tile_source<NT>(a, vd, t, skey, sid);
+    const TileSrc src = tile_source<NT>(a, vd, t);
     bool active = valid;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
         if (tid < nc) {
             int32_t g;
-            if (src.mode == 1) g = sid[base + tid];
-            else if (src.mode == 0) g = a.ws.tile_gauss[src.start + base + tid];
+            if (src.mode != 2) g = a.ws.tile_gauss[src.start + base + tid];
             else g = base + tid;
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
@@ -242,7 +198,8 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             // order) starts beyond its K-th depth can stop for good
             if (active && src.mode == 1 && nc == NT && base + NT < src.count) {
                 // the first candidate of the next chunk bounds everything after it
-                const float nxt = skey[base + NT];
+                const int32_t gn = __ldg(a.ws.tile_gauss + src.start + base + NT);
+                const float nxt = __ldg(&a.ws.rec[4 * (vb + gn) + 3].w);
                 if (nxt > kmax) active = false;
             }
         }
@@ -352,7 +309,7 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             }
         }
     }
-    if (C >= 16) {
+    if (C >= 64) {
         // wide attributes: the warp blends one pixel at a time, lanes over channels
         for (int p = 0; p < 32; ++p) {
             const int irow = ty * TH + 2 * warp + (p >> 4), jcol = tx * kTileW + (p & 15);
@@ -370,13 +327,37 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             }
         }
     } else if (valid) {
-        for (int c = 0; c < C; ++c) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int s = 0; s < KM; ++s)
-                if (s >= KM - K && s - (KM - K) < n) acc = fmaf(Wt[s], __ldg(vd.attr + (int64_t)id[s] * C + c), acc);
-            vd.image[pix * C + c] = acc;
+        // this lane's list from the warp's staging area (runtime loop: no register arrays)
+        const int32_t* myid = reinterpret_cast<const int32_t*>(stg(lane * L));
+        const bool v4 = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(vd.attr) |
+                                          reinterpret_cast<uintptr_t>(vd.image)) & 15) == 0;
+        if (v4) {
+            for (int c = 0; c < C; c += 4) {
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k = 0; k < n; ++k) {
+                    const int x = lane * L + k;
+                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(x));
+                    const float w = *stg(nblk * 128 + x);
+                    const float4 a4 = __ldg(reinterpret_cast<const float4*>(vd.attr + (int64_t)g * C + c));
+                    acc.x = fmaf(w, a4.x, acc.x);
+                    acc.y = fmaf(w, a4.y, acc.y);
+                    acc.z = fmaf(w, a4.z, acc.z);
+                    acc.w = fmaf(w, a4.w, acc.w);
+                }
+                *reinterpret_cast<float4*>(vd.image + pix * C + c) = acc;
+            }
+        } else {
+            for (int c = 0; c < C; ++c) {
+                float acc = 0.0f;
+                for (int k = 0; k < n; ++k) {
+                    const int x = lane * L + k;
+                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(x));
+                    acc = fmaf(*stg(nblk * 128 + x), __ldg(vd.attr + (int64_t)g * C + c), acc);
+                }
+                vd.image[pix * C + c] = acc;
+            }
         }
+        (void)myid;
     }
 }
 
@@ -399,8 +380,6 @@ __device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
     extern __shared__ float4 smem[];
     float4* stage = smem;
     int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
-    float* skey = reinterpret_cast<float*>(sgid + NT);
-    int32_t* sid = reinterpret_cast<int32_t*>(skey + kSortMax);
 
     const int v = view_of_tile(a.views, a.hdr->nviews, t);
     const ViewDesc& vd = a.views[v];
@@ -421,14 +400,13 @@ __device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
     int32_t* li = a.ws.gid + gpix * (int64_t)a.ws.gen_L;
     int n = 0;
 
-    const TileSrc src = tile_source<NT>(a, vd, t, skey, sid);
+    const TileSrc src = tile_source<NT>(a, vd, t);
     bool active = valid;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
         if (tid < nc) {
             int32_t g;
-            if (src.mode == 1) g = sid[base + tid];
-            else if (src.mode == 0) g = a.ws.tile_gauss[src.start + base + tid];
+            if (src.mode != 2) g = a.ws.tile_gauss[src.start + base + tid];
             else g = base + tid;
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
@@ -517,8 +495,8 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a) {
 
 size_t render_smem_bytes(int KM, int TH) {
     const int NT = 16 * TH;
-    const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)kSortMax * 8 + (size_t)NT * TH * 2 +
-                          (size_t)NT * (NT / 32) * 4 + (size_t)KM * NT * 8;
+    const size_t phase1 = (size_t)NT * 64 + (size_t)NT * 4 + (size_t)NT * TH * 2 + (size_t)NT * (NT / 32) * 4 +
+                          (size_t)KM * NT * 8;
     const size_t phase2 = (size_t)KM * NT * 16;
     return phase1 > phase2 ? phase1 : phase2;
 }

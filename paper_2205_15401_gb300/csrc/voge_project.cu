@@ -219,6 +219,64 @@ __global__ void __launch_bounds__(256) k_scatter(Args a) {
     }
 }
 
+// Depth order of each tile's candidate list (ascending lower bound of l), so
+// that a pixel can stop once no later candidate can enter its list.  One warp
+// per tile, bitonic sort in the warp's shared memory (lists of at most
+// kSortMax entries; longer lists stay unsorted and are traced in full).
+__device__ __forceinline__ bool tile_sorted(int use_thresh, int plain, int cnt, int64_t off, int64_t cap) {
+    return use_thresh && !plain && cnt > 1 && cnt <= kSortMax && off + cnt <= cap;
+}
+
+__global__ void __launch_bounds__(128) k_sort_tiles(Args a) {
+    extern __shared__ float sk_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* key = sk_smem + wib * 2 * kSortMax;
+    int32_t* val = reinterpret_cast<int32_t*>(key + kSortMax);
+    const int nv = a.hdr->nviews, total = a.hdr->total_tiles;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < total; t += nwarps) {
+        const int cnt = a.ws.tile_cnt[t];
+        const int off = a.ws.tile_off[t];
+        const ViewDesc& vd = a.views[view_of_tile(a.views, nv, t)];
+        if (!tile_sorted(vd.use_thresh, vd.plain, cnt, off, a.ws.bin_cap)) continue;
+        int n2 = 1;
+        while (n2 < cnt) n2 <<= 1;
+        const int64_t vb = vd.rec_base;
+        for (int x = lane; x < n2; x += 32) {
+            if (x < cnt) {
+                const int32_t g = a.ws.tile_gauss[off + x];
+                key[x] = __ldg(&a.ws.rec[4 * (vb + g) + 3].w);
+                val[x] = g;
+            } else {
+                key[x] = INFINITY;
+                val[x] = -1;
+            }
+        }
+        __syncwarp();
+        for (int k = 2; k <= n2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int x = lane; x < n2; x += 32) {
+                    const int y = x ^ j;
+                    if (y > x) {
+                        const bool up = (x & k) == 0;
+                        const float kx = key[x], ky = key[y];
+                        if ((kx > ky) == up) {
+                            key[x] = ky;
+                            key[y] = kx;
+                            const int32_t tv = val[x];
+                            val[x] = val[y];
+                            val[y] = tv;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int x = lane; x < cnt; x += 32) a.ws.tile_gauss[off + x] = val[x];
+        __syncwarp();
+    }
+}
+
 // Projection of every (view, Gaussian) record, then (with count_tiles) the
 // tile scan and scatter.  Grid-stride kernels: `grid` blocks of 256 threads
 // cover any number of records read from the batch header.
@@ -237,6 +295,12 @@ cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args
         {
             TraceScope tr("k_scatter", s);
             k_scatter<<<grid, 256, 0, s>>>(a);
+        }
+        {
+            TraceScope tr("k_sort_tiles", s);
+            const int smem = 4 * 2 * kSortMax * 4;
+            cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_sort_tiles<<<grid, 128, smem, s>>>(a);
         }
         return cudaPeekAtLastError();
     }
