@@ -228,7 +228,29 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
         const int k = s - (KM - K);
         id[s] = (k >= 0 && k < n) ? sli[k * NT + tid] : -1;
     }
-    __syncthreads();  // staging area becomes the j-stream
+    __syncthreads();  // selection buffers are free from here on
+
+    // ---------------- index output ----------------
+    // Each warp covers two 16-pixel row segments of the tile; a segment's
+    // lists are contiguous in memory ([pixel][L]).  The warp stages its 32
+    // lists in its own shared-memory columns (blocks of 32 float4) and writes
+    // each segment with consecutive lanes on consecutive words.
+    const int L = vd.L, C = vd.C;
+    const int lane = tid & 31, warp = tid >> 5;
+    auto stg = [&](int x) -> float* { return reinterpret_cast<float*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127); };
+    const int ncols = min(kTileW, W - tx * kTileW);
+#pragma unroll
+    for (int s = 0; s < KM; ++s)
+        if (s >= KM - K) *reinterpret_cast<int32_t*>(stg(lane * L + (s - (KM - K)))) = id[s];
+    __syncwarp();
+#pragma unroll
+    for (int rw = 0; rw < 2; ++rw) {
+        const int irow = ty * TH + 2 * warp + rw;
+        if (irow >= H) continue;
+        int32_t* di = vd.index + ((int64_t)irow * W + tx * kTileW) * L;
+        for (int x = lane; x < ncols * L; x += 32) di[x] = *reinterpret_cast<const int32_t*>(stg(rw * 16 * L + x));
+    }
+    __syncwarp();
 
     // ---------------- fine pass ----------------
     // kept entries occupy slots [KM - K, KM - K + n) in ascending (l, index)
@@ -258,57 +280,37 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
         }
     }
+    // W_k = T_k a_k, written over A_k
     const float ntl = -vd.tau * kLog2e;
-    float Wt[KM];
     {
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
-            Wt[s] = 0.0f;
             if (s >= KM - K && s - (KM - K) < n) {
                 const float am = jst[e * NT + tid].w;
-                Wt[s] = ex2_approx(ntl * A[s]) * (2.0f * am);
+                A[s] = ex2_approx(ntl * A[s]) * (2.0f * am);
                 ++e;
+            } else {
+                A[s] = 0.0f;
             }
         }
     }
-    // ---------------- outputs ----------------
-    // Each warp covers two 16-pixel row segments of the tile; a segment's
-    // lists are contiguous in memory ([pixel][L]).  The warp stages its 32
-    // lists in the shared-memory columns its own lanes used for the j-stream
-    // (blocks of 32 float4, one per list slot e) and writes each segment with
-    // consecutive lanes on consecutive words.
-    const int L = vd.L, C = vd.C;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int nblk = (L + 3) >> 2;  // blocks of 128 words holding 32 x L entries
-    auto stg = [&](int x) -> float* { return reinterpret_cast<float*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127); };
+    // ---------------- weights and image ----------------
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        if (s >= KM - K) {
-            const int k = s - (KM - K);
-            const bool real = k < n;
-            *reinterpret_cast<int32_t*>(stg(lane * L + k)) = real ? id[s] : -1;
-            *stg(nblk * 128 + lane * L + k) = Wt[s];
-        }
-    }
+    for (int s = 0; s < KM; ++s)
+        if (s >= KM - K) *stg(lane * L + (s - (KM - K))) = A[s];
     __syncwarp();
-    {
-        const int ncols = min(kTileW, W - tx * kTileW);
+    if (vd.weights) {
 #pragma unroll
         for (int rw = 0; rw < 2; ++rw) {
             const int irow = ty * TH + 2 * warp + rw;
             if (irow >= H) continue;
-            const int64_t first = (int64_t)irow * W + tx * kTileW;
-            const int cnt = ncols * L;
-            int32_t* di = vd.index + first * L;
-            float* dw = vd.weights ? vd.weights + first * L : nullptr;
-            for (int x = lane; x < cnt; x += 32) {
-                di[x] = *reinterpret_cast<const int32_t*>(stg(rw * 16 * L + x));
-                if (dw) dw[x] = *stg(nblk * 128 + rw * 16 * L + x);
-            }
+            float* dw = vd.weights + ((int64_t)irow * W + tx * kTileW) * L;
+            for (int x = lane; x < ncols * L; x += 32) dw[x] = *stg(rw * 16 * L + x);
         }
     }
+    // the blend reads the lists back from the index output this warp wrote
     if (C >= 64) {
         // wide attributes: the warp blends one pixel at a time, lanes over channels
         for (int p = 0; p < 32; ++p) {
@@ -319,25 +321,23 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 const int c = c0 + lane;
                 float acc = 0.0f;
                 for (int k = 0; k < L; ++k) {
-                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(p * L + k));
+                    const int32_t g = vd.index[pp * L + k];
                     if (g < 0) break;
-                    if (c < C) acc = fmaf(*stg(nblk * 128 + p * L + k), __ldg(vd.attr + (int64_t)g * C + c), acc);
+                    if (c < C) acc = fmaf(*stg(p * L + k), __ldg(vd.attr + (int64_t)g * C + c), acc);
                 }
                 if (c < C) vd.image[pp * C + c] = acc;
             }
         }
     } else if (valid) {
-        // this lane's list from the warp's staging area (runtime loop: no register arrays)
-        const int32_t* myid = reinterpret_cast<const int32_t*>(stg(lane * L));
+        // this lane's list: indices from the index output, weights from the staging area
         const bool v4 = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(vd.attr) |
                                           reinterpret_cast<uintptr_t>(vd.image)) & 15) == 0;
         if (v4) {
             for (int c = 0; c < C; c += 4) {
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int k = 0; k < n; ++k) {
-                    const int x = lane * L + k;
-                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(x));
-                    const float w = *stg(nblk * 128 + x);
+                    const int32_t g = vd.index[pix * L + k];
+                    const float w = *stg(lane * L + k);
                     const float4 a4 = __ldg(reinterpret_cast<const float4*>(vd.attr + (int64_t)g * C + c));
                     acc.x = fmaf(w, a4.x, acc.x);
                     acc.y = fmaf(w, a4.y, acc.y);
@@ -350,14 +350,12 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             for (int c = 0; c < C; ++c) {
                 float acc = 0.0f;
                 for (int k = 0; k < n; ++k) {
-                    const int x = lane * L + k;
-                    const int32_t g = *reinterpret_cast<const int32_t*>(stg(x));
-                    acc = fmaf(*stg(nblk * 128 + x), __ldg(vd.attr + (int64_t)g * C + c), acc);
+                    const int32_t g = vd.index[pix * L + k];
+                    acc = fmaf(*stg(lane * L + k), __ldg(vd.attr + (int64_t)g * C + c), acc);
                 }
                 vd.image[pix * C + c] = acc;
             }
         }
-        (void)myid;
     }
 }
 
