@@ -52,7 +52,7 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const 
     out[8] = fmaf(dqt, V2 * V2, fmaf(lb, V2, db));
 }
 
-template <int KM, int TH>
+template <int KM, int TH, bool COOP>
 __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
@@ -95,33 +95,40 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         }
     }
     __syncwarp();
-    int32_t id[KM];
-#pragma unroll
-    for (int s = 0; s < KM; ++s) id[s] = (s >= KM - K) ? *stg(lane * L + (s - (KM - K))) : -1;
-    __syncwarp();
+    // Kept entries occupy slots [KM - K, KM - K + n); slot s holds list
+    // position k = s - (KM - K).  The indices live in registers only while
+    // the entries are set up; later stages reload them from the list (the
+    // rows were just read, so these hit in cache).
     float hi[KM], lo[KM], dA[KM], dl[KM];
     int n = 0;
-    bool open = valid;  // lanes outside the image keep no entries but stay for the warp-wide steps
+    {
+        int32_t id[KM];
 #pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        hi[s] = 0.0f;
-        lo[s] = 0.0f;
-        dA[s] = 0.0f;
-        dl[s] = 0.0f;
-        const int32_t g = id[s];
-        if (s >= KM - K && open && g >= 0 && g < N) {
-            float4 r0, r1, r2, r3;
-            load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
-            const Entry e = entry_px(r0, r1, r2, r3, px, py);
-            hi[s] = e.hi;
-            lo[s] = e.lo;
-            jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
-            ++n;
-        } else {
-            if (s >= KM - K) open = false;
-            id[s] = -1;
+        for (int s = 0; s < KM; ++s) id[s] = (s >= KM - K) ? *stg(lane * L + (s - (KM - K))) : -1;
+        __syncwarp();
+        bool open = valid;  // lanes outside the image keep no entries but stay for the warp-wide steps
+#pragma unroll
+        for (int s = 0; s < KM; ++s) {
+            hi[s] = 0.0f;
+            lo[s] = 0.0f;
+            dA[s] = 0.0f;
+            dl[s] = 0.0f;
+            const int32_t g = id[s];
+            if (s >= KM - K && open && g >= 0 && g < N) {
+                float4 r0, r1, r2, r3;
+                load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+                const Entry e = entry_px(r0, r1, r2, r3, px, py);
+                hi[s] = e.hi;
+                lo[s] = e.lo;
+                jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
+                ++n;
+            } else if (s >= KM - K) {
+                open = false;
+            }
         }
     }
+    const int32_t* li = vd.index_in + pix * L;
+    auto kept = [&](int s) { return s >= KM - K && s - (KM - K) < n; };
     // loop 1: A_k
     float A[KM];
 #pragma unroll
@@ -136,24 +143,52 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
         }
     }
-    // T, W, attribute gradient, dA
+    // T, W, dA and the attribute gradient dL/dc_g += W_k dL/dI.  With
+    // C >= 8 the attribute gradient is scattered warp-cooperatively: for one
+    // list slot the lanes cover (source lane, channel) pairs, so one
+    // reduction instruction updates whole rows of grad_attr instead of 32
+    // scattered words per channel.  Narrow attributes (C < 8) keep one
+    // reduction per lane and channel, which issues fewer instructions.
     const float ntl = -tau * kLog2e;
     const float* gp = vd.grad_image + pix * C;
+    constexpr bool coop = COOP;
+    const int spi = C <= 32 ? 32 / C : 1;  // source lanes per step
+    const int sub = C <= 32 ? lane / C : 0;
+    const int cc = C <= 32 ? lane - sub * C : lane;
+    const int64_t pbase = (int64_t)(ty * TH + 2 * warp) * W + tx * kTileW;
     {
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
-            if (id[s] >= 0) {
-                const float Wk = ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
-                const float* ck = attr + (int64_t)id[s] * C;
+            float Wk = 0.0f;
+            int32_t g = -1;
+            if (kept(s)) {
+                g = __ldg(li + (s - (KM - K)));
+                Wk = ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
+                const float* ck = attr + (int64_t)g * C;
                 float G = 0.0f;
                 for (int c = 0; c < C; ++c) {
                     const float gc = __ldg(gp + c);
                     G = fmaf(gc, __ldg(ck + c), G);
-                    if (grad_attr) atomicAdd(grad_attr + (int64_t)id[s] * C + c, Wk * gc);
+                    if (grad_attr && !coop) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
                 }
                 dA[s] = -tau * G * Wk;
                 ++e;
+            }
+            if (grad_attr && coop) {
+                const unsigned m = __ballot_sync(0xffffffffu, g >= 0);
+                const int top = 32 - __clz(m);
+#pragma unroll 1
+                for (int s0 = 0; s0 < top; s0 += spi) {
+                    const int src = s0 + sub;
+                    const int32_t gs = __shfl_sync(0xffffffffu, g, src & 31);
+                    const float ws = __shfl_sync(0xffffffffu, Wk, src & 31);
+                    if (sub < spi && src < 32 && gs >= 0) {
+                        const float* gsrc = vd.grad_image + (pbase + (src >> 4) * W + (src & 15)) * C;
+                        float* dst = grad_attr + (int64_t)gs * C;
+                        for (int c = cc; c < C; c += 32) atomicAdd(dst + c, ws * __ldg(gsrc + c));
+                    }
+                }
             }
         }
     }
@@ -184,10 +219,10 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
-            if (id[s] >= 0) {
+            if (kept(s)) {
                 const float4 J = jst[e * NT + tid];
                 float4 r0, r1, r2, r3;
-                const int64_t o = vb + id[s];
+                const int64_t o = vb + __ldg(li + (s - (KM - K)));
                 load_rec(a.ws.rec, o, r0, r1, r2, r3);
                 const Trace tr = trace_px(r0, r1, r2, r3, px, py);
                 const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
@@ -212,7 +247,9 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
     for (;;) {
         const int t = next_tile(a, 0, &s_slot);
         if (t < 0) return;
-        backward_tile<KM, TH>(a, t);
+        // wide attributes take the warp-cooperative attribute scatter
+        if (a.views[view_of_tile(a.views, a.hdr->nviews, t)].C >= 8) backward_tile<KM, TH, true>(a, t);
+        else backward_tile<KM, TH, false>(a, t);
     }
 }
 
