@@ -11,7 +11,7 @@
 #include "voge_trace.cuh"
 
 namespace voge {
-cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args& a);
+cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a);
@@ -239,7 +239,7 @@ int upload_and_project(const voge_camera* cams, const voge_params* p, const Layo
     const int count_tiles = bin && !(p->flags & VOGE_FLAG_PLAIN);
     if (count_tiles && cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(l.total_tiles + 1), s) != cudaSuccess)
         return VOGE_ERR_CUDA;
-    return launch_project(record_grid((int64_t)p->B * p->N), count_tiles, s, a) == cudaSuccess ? VOGE_OK
+    return launch_project(record_grid((int64_t)p->B * p->N), l.total_tiles, count_tiles, s, a) == cudaSuccess ? VOGE_OK
                                                                                                 : VOGE_ERR_CUDA;
 }
 

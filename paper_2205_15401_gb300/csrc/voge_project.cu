@@ -227,60 +227,63 @@ __device__ __forceinline__ bool tile_sorted(int use_thresh, int plain, int cnt, 
     return use_thresh && !plain && cnt > 1 && cnt <= kSortMax && off + cnt <= cap;
 }
 
-__global__ void __launch_bounds__(128) k_sort_tiles(Args a) {
-    extern __shared__ float sk_smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float* key = sk_smem + wib * 2 * kSortMax;
-    int32_t* val = reinterpret_cast<int32_t*>(key + kSortMax);
+// One block sorts one tile list at a time.  Each entry is one 64-bit word,
+// (order-preserving bits of lmin) << 32 | index, so one compare orders by
+// (lmin, index) and a swap moves key and index together.  The list is padded
+// with all-ones words to a power of two; the bitonic network gives every
+// thread n/2/256 compare-exchanges per stage, with a block barrier between
+// stages.
+constexpr int kSortThreads = 256;
+
+__device__ __forceinline__ uint64_t sort_word(float key, int32_t g) {
+    uint32_t b = __float_as_uint(key);
+    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ((uint64_t)b << 32) | (uint32_t)g;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
+    __shared__ uint64_t w[kSortMax];
+    const int tid = threadIdx.x;
     const int nv = a.hdr->nviews, total = a.hdr->total_tiles;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < total; t += nwarps) {
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int cnt = a.ws.tile_cnt[t];
         const int off = a.ws.tile_off[t];
         const ViewDesc& vd = a.views[view_of_tile(a.views, nv, t)];
-        if (!tile_sorted(vd.use_thresh, vd.plain, cnt, off, a.ws.bin_cap)) continue;
-        int n2 = 1;
+        if (!tile_sorted(vd.use_thresh, vd.plain, cnt, off, a.ws.bin_cap)) continue;  // uniform in the block
+        int n2 = 2;
         while (n2 < cnt) n2 <<= 1;
         const int64_t vb = vd.rec_base;
-        for (int x = lane; x < n2; x += 32) {
+        for (int x = tid; x < n2; x += kSortThreads) {
+            uint64_t v = ~0ull;
             if (x < cnt) {
                 const int32_t g = a.ws.tile_gauss[off + x];
-                key[x] = __ldg(&a.ws.rec[4 * (vb + g) + 3].w);
-                val[x] = g;
-            } else {
-                key[x] = INFINITY;
-                val[x] = -1;
+                v = sort_word(__ldg(&a.ws.rec[4 * (vb + g) + 3].w), g);
             }
+            w[x] = v;
         }
-        __syncwarp();
+        __syncthreads();
         for (int k = 2; k <= n2; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int x = lane; x < n2; x += 32) {
-                    const int y = x ^ j;
-                    if (y > x) {
-                        const bool up = (x & k) == 0;
-                        const float kx = key[x], ky = key[y];
-                        if ((kx > ky) == up) {
-                            key[x] = ky;
-                            key[y] = kx;
-                            const int32_t tv = val[x];
-                            val[x] = val[y];
-                            val[y] = tv;
-                        }
-                    }
+                for (int q = tid; q < (n2 >> 1); q += kSortThreads) {
+                    const int x = 2 * q - (q & (j - 1));  // lower element of pair q at distance j
+                    const int y = x + j;
+                    const uint64_t wx = w[x], wy = w[y];
+                    const bool sw = (wx > wy) == ((x & k) == 0);
+                    w[x] = sw ? wy : wx;
+                    w[y] = sw ? wx : wy;
                 }
-                __syncwarp();
+                __syncthreads();
             }
         }
-        for (int x = lane; x < cnt; x += 32) a.ws.tile_gauss[off + x] = val[x];
-        __syncwarp();
+        for (int x = tid; x < cnt; x += kSortThreads) a.ws.tile_gauss[off + x] = (int32_t)(uint32_t)w[x];
+        __syncthreads();  // the next tile reuses w
     }
 }
 
 // Projection of every (view, Gaussian) record, then (with count_tiles) the
 // tile scan and scatter.  Grid-stride kernels: `grid` blocks of 256 threads
 // cover any number of records read from the batch header.
-cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args& a) {
+cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a) {
     {
         TraceScope tr("k_project", s);
         k_project<<<grid, 256, 0, s>>>(a, count_tiles);
@@ -297,10 +300,10 @@ cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args
             k_scatter<<<grid, 256, 0, s>>>(a);
         }
         {
+            // one block per tile (grid-stride beyond 8 blocks per SM)
             TraceScope tr("k_sort_tiles", s);
-            const int smem = 4 * 2 * kSortMax * 4;
-            cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k_sort_tiles<<<grid, 128, smem, s>>>(a);
+            const int sgrid = tiles < 1 ? 1 : (tiles < 152 * 8 ? tiles : 152 * 8);
+            k_sort_tiles<<<sgrid, kSortThreads, 0, s>>>(a);
         }
         return cudaPeekAtLastError();
     }

@@ -30,7 +30,7 @@
 #include "voge_trace.cuh"
 
 namespace voge {
-cudaError_t launch_project(int grid, int count_tiles, cudaStream_t s, const Args& a);
+cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a);
@@ -341,7 +341,7 @@ cudaError_t issue_tick(voge_server* S, TickSlot& ts, uint32_t mask) {
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(S->max_tiles + 1), s);
     if (e != cudaSuccess) return e;
-    e = launch_project(S->grid_records, 1, s, a);
+    e = launch_project(S->grid_records, (int)std::min<int64_t>(S->max_tiles, (int64_t)S->grid_records * 8), 1, s, a);
     if (e != cudaSuccess) return e;
     for (int c = 0; c < kClasses; ++c) {
         if (!(mask & (1u << c))) continue;

@@ -99,6 +99,33 @@ def test_tiled_equals_plain_bit_exact():
     np.testing.assert_array_equal(w_t, w_p)
 
 
+def _centres_per_tile(cam, means, tile_w=16, tile_h=16):
+    """Projected centres per 16x16 tile: a lower bound of each tile's candidate count."""
+    X = means @ np.asarray(cam["R"]).T + np.asarray(cam["T"])
+    z = X[:, 2]
+    u = cam["F"] * X[:, 0] / z + cam["Ox"]
+    v = cam["F"] * X[:, 1] / z + cam["Oy"]
+    ok = (z > 0) & (u >= 0) & (u < cam["W"]) & (v >= 0) & (v < cam["H"])
+    tiles = (v[ok] // tile_h).astype(int) * ((cam["W"] + tile_w - 1) // tile_w) + (u[ok] // tile_w).astype(int)
+    return np.bincount(tiles)
+
+
+@pytest.mark.parametrize("N,lo", [(1000, 128), (2500, 512), (6000, 1024), (12000, 2048)])
+def test_long_tile_lists_sorted_exactly(N, lo):
+    """Tiles with hundreds to thousands of candidates (every sort size class,
+    and lists past the sorted maximum) give the same bits as no binning."""
+    sc = scenes.fit_8x512(seed=21, N=N, B=1, side=64)
+    cams, m, p, a = scene_inputs(sc)
+    assert _centres_per_tile(cams[0], m).max() > lo
+    from paper_2205_15401_gb300.voge import VOGE_FLAG_PLAIN
+
+    _, _, img_t, w_t, idx_t = gpu_forward(cams, m, p, a, 20, 1.0, 0.01)
+    _, _, img_p, w_p, idx_p = gpu_forward(cams, m, p, a, 20, 1.0, 0.01, flags=VOGE_FLAG_PLAIN)
+    np.testing.assert_array_equal(idx_t, idx_p)
+    np.testing.assert_array_equal(img_t, img_p)
+    np.testing.assert_array_equal(w_t, w_p)
+
+
 def test_bin_overflow_falls_back_exactly():
     sc = scenes.posefit_256(seed=3, N=3000, C=4)
     cams, m, p, a = scene_inputs(sc)
