@@ -151,43 +151,44 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 smask[w * NT + tid] = m;
             }
             // 2) each lane walks its own hits: lanes of a warp trace different
-            //    candidates at the same time instead of the union of all hits
+            //    candidates at the same time instead of the union of all hits.
+            //    One cursor runs over all mask words, so the warp iterates as
+            //    often as its busiest lane has hits in the chunk.
             const float* lmin = reinterpret_cast<const float*>(stage + 3 * NT) + 3;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                uint32_t m = active ? smask[w * NT + tid] : 0u;
-                while (m) {
-                    const int q = w * 32 + __ffs(m) - 1;
-                    m &= m - 1;
-                    if (src.mode == 1 && lmin[4 * q] > kmax) {
-                        active = false;  // sorted by lower bound: nothing later can enter
-                        m = 0;
-                        break;
+            int w = 0;
+            uint32_t m = smask[tid];
+            for (;;) {
+                while (m == 0 && w < NW - 1) m = smask[++w * NT + tid];
+                if (m == 0) break;
+                const int q = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                if (src.mode == 1 && lmin[4 * q] > kmax) {
+                    active = false;  // sorted by lower bound: nothing later can enter
+                    break;
+                }
+                const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q], r3 = stage[3 * NT + q];
+                const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
+                if (l > 0.0f) {
+                    const int32_t g = sgid[q];
+                    int slot = -1;
+                    if (n < K) {
+                        slot = n++;
+                    } else if (l < kmax || (l == kmax && g < gmax)) {
+                        slot = smax;
                     }
-                    const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q], r3 = stage[3 * NT + q];
-                    const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
-                    if (l > 0.0f) {
-                        const int32_t g = sgid[q];
-                        int slot = -1;
-                        if (n < K) {
-                            slot = n++;
-                        } else if (l < kmax || (l == kmax && g < gmax)) {
-                            slot = smax;
-                        }
-                        if (slot >= 0) {
-                            slk[slot * NT + tid] = l;
-                            sli[slot * NT + tid] = g;
-                            if (n == K) {  // full: find the farthest entry, the bar for later candidates
-                                kmax = -INFINITY;
-                                gmax = -1;
-                                for (int s2 = 0; s2 < K; ++s2) {
-                                    const float x = slk[s2 * NT + tid];
-                                    const int32_t y = sli[s2 * NT + tid];
-                                    if (x > kmax || (x == kmax && y > gmax)) {
-                                        kmax = x;
-                                        gmax = y;
-                                        smax = s2;
-                                    }
+                    if (slot >= 0) {
+                        slk[slot * NT + tid] = l;
+                        sli[slot * NT + tid] = g;
+                        if (n == K) {  // full: find the farthest entry, the bar for later candidates
+                            kmax = -INFINITY;
+                            gmax = -1;
+                            for (int s2 = 0; s2 < K; ++s2) {
+                                const float x = slk[s2 * NT + tid];
+                                const int32_t y = sli[s2 * NT + tid];
+                                if (x > kmax || (x == kmax && y > gmax)) {
+                                    kmax = x;
+                                    gmax = y;
+                                    smax = s2;
                                 }
                             }
                         }
