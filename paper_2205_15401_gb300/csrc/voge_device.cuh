@@ -264,19 +264,26 @@ __device__ __forceinline__ void topk_insert(float (&key)[KM], int32_t (&id)[KM],
     id[0] = lt[0] ? g : id[0];
 }
 
-// Column interval of each tile row in which the candidate test can pass.
-// Per row the test qb < Qeta b is the quadratic inequality
+// Pixels of each tile row in which the candidate test can pass.  Per row
+// the test qb < Qeta b is the quadratic inequality
 //   h00 du^2 + 2 (h01 dv + hx) du + (h11 dv^2 + 2 hy dv + h22) < 0,
 // an interval of du whenever h00 > 0.  The interval is widened by 1 pixel
 // plus 2% of its half-width, so it never excludes a pixel that the exact
-// per-pixel test keeps; rows with h00 <= 0 (or no threshold) are left whole.
-// Output: tile-local columns packed as lo | hi << 8 (lo > hi: empty row).
-constexpr uint16_t kRowEmpty = 0x00ffu;
-constexpr uint16_t kRowFull = (uint16_t)(15u << 8);
+// per-pixel test keeps (this margin also covers the approximate square root
+// and reciprocal used here); rows with h00 <= 0 (or no threshold) are left
+// whole.  Output: one 16-bit mask per row, bit c set for tile column c.
+constexpr uint16_t kRowEmpty = 0x0000u;
+constexpr uint16_t kRowFull = 0xffffu;
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 template <int TH>
-__device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
-                                              float Q, int tx, int ty, uint16_t* out, int stride) {
+__device__ __forceinline__ void row_masks(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                          float Q, int tx, int ty, uint16_t* out, int stride) {
     const float h00 = fmaf(-Q, r1.w, r2.z);
     if (!(h00 > 0.0f) || !(Q < INFINITY)) {
 #pragma unroll
@@ -286,7 +293,7 @@ __device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1
     const float h01 = 0.5f * fmaf(-Q, r2.x, r2.w);
     const float h11 = fmaf(-Q, r2.y, r3.x);
     const float hx = -Q * r1.y, hy2 = -2.0f * Q * r1.z, h22 = -Q * r1.x;
-    const float ih = 1.0f / h00;
+    const float ih = rcp_approx(h00);
     const float uoff = r0.x - ((float)(tx * kTileW) + 0.5f);  // centre relative to tile column 0
     const float row0 = (float)(ty * TH) + 0.5f;
 #pragma unroll
@@ -296,17 +303,13 @@ __device__ __forceinline__ void row_intervals(const float4& r0, const float4& r1
         const float Cp = fmaf(fmaf(h11, dv, hy2), dv, h22);
         const float disc = fmaf(Bp, Bp, -h00 * Cp);
         const float scale = fmaf(Bp, Bp, fabsf(h00 * Cp));
-        uint16_t code = kRowEmpty;
-        if (disc > -1e-3f * scale) {
-            const float w = sqrtf(fmaxf(disc, 0.0f)) * ih;
-            const float c = uoff - Bp * ih;
-            const float m = fmaf(0.02f, w, 1.0f);
-            const float klo = ceilf(c - w - m), khi = floorf(c + w + m);
-            const int lo = (int)fminf(fmaxf(klo, 0.0f), 16.0f);
-            const int hi = (int)fmaxf(fminf(khi, 15.0f), -1.0f);
-            if (lo <= hi) code = (uint16_t)(lo | (hi << 8));
-        }
-        out[rr * stride] = code;
+        const float w = sqrt_approx(fmaxf(disc, 0.0f)) * ih;
+        const float c = uoff - Bp * ih;
+        const float m = fmaf(0.02f, w, 1.0f);
+        const int lo = (int)fminf(fmaxf(ceilf(c - w - m), 0.0f), 16.0f);
+        const int hi = (int)fmaxf(fminf(floorf(c + w + m), 15.0f), -1.0f);
+        const uint32_t bits = (0xffffu >> (15 - max(hi, 0))) & (0xffffu << lo);
+        out[rr * stride] = (disc > -1e-3f * scale && lo <= hi) ? (uint16_t)bits : kRowEmpty;
     }
 }
 

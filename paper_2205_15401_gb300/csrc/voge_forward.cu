@@ -121,31 +121,34 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
 #pragma unroll
                 for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;
             } else {
-                row_intervals<TH>(r0, r1, r2, r3, Qeta, tx, ty, siv + tid, NT);
+                row_masks<TH>(r0, r1, r2, r3, Qeta, tx, ty, siv + tid, NT);
             }
-        } else if (tid < ((nc + 3) & ~3)) {
+        } else if (tid < ((nc + 7) & ~7)) {
 #pragma unroll
-            for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;  // pad the last group of four
+            for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;  // pad the last group of eight
         }
         __syncthreads();
         if (active) {
-            // 1) this pixel's hits in the chunk, as a bit mask (cheap, uniform)
+            // 1) this pixel's hits in the chunk, as a bit mask (cheap, uniform):
+            //    bit jl of each candidate's row mask, eight candidates per
+            //    16-byte read, gathered with shifts into one 32-bit word per
+            //    32 candidates
             constexpr int NW = NT / 32;
             const int jl = tid & 15, rr = tid >> 4;
-            const uint2* ivrow = reinterpret_cast<const uint2*>(siv + rr * NT);
+            const uint4* ivrow = reinterpret_cast<const uint4*>(siv + rr * NT);
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 uint32_t m = 0;
 #pragma unroll
-                for (int g4 = 0; g4 < 8; ++g4) {
-                    const int q0 = w * 32 + g4 * 4;
+                for (int g8 = 0; g8 < 4; ++g8) {
+                    const int q0 = w * 32 + g8 * 8;
                     if (q0 < nc) {
-                        const uint2 iv4 = ivrow[q0 >> 2];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t iv = ((u < 2 ? iv4.x : iv4.y) >> (16 * (u & 1))) & 0xffffu;
-                            m |= (jl >= (int)(iv & 255u) && jl <= (int)(iv >> 8)) ? (1u << (g4 * 4 + u)) : 0u;
-                        }
+                        const uint4 x = ivrow[q0 >> 3];
+                        // candidate 2i sits in bits 0-15 of word i, candidate 2i+1 in bits 16-31
+                        const uint32_t t = ((x.x >> jl) & 0x10001u) | (((x.y >> jl) & 0x10001u) << 2) |
+                                           (((x.z >> jl) & 0x10001u) << 4) | (((x.w >> jl) & 0x10001u) << 6);
+                        const uint32_t v = (t & 0x55u) | ((t >> 15) & 0xaau);
+                        m |= v << (g8 * 8);
                     }
                 }
                 smask[w * NT + tid] = m;
