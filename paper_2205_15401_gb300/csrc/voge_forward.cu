@@ -94,6 +94,25 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
     int32_t gmax = INT32_MAX;
 
     const TileSrc src = tile_source<NT>(a, vd, t);
+    if (src.count == 0) {
+        // no candidate reaches this tile: empty lists, zero weights and image,
+        // each warp writing its two row segments
+        const int lane = tid & 31, warp = tid >> 5;
+        const int L = vd.L, C = vd.C;
+        const int ncols = min(kTileW, W - tx * kTileW);
+#pragma unroll
+        for (int rw = 0; rw < 2; ++rw) {
+            const int irow = ty * TH + 2 * warp + rw;
+            if (irow >= H) continue;
+            const int64_t p0 = (int64_t)irow * W + tx * kTileW;
+            for (int x = lane; x < ncols * L; x += 32) {
+                vd.index[p0 * L + x] = -1;
+                if (vd.weights) vd.weights[p0 * L + x] = 0.0f;
+            }
+            for (int x = lane; x < ncols * C; x += 32) vd.image[p0 * C + x] = 0.0f;
+        }
+        return;
+    }
     bool active = valid;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
@@ -332,6 +351,23 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 if (c < C) vd.image[pp * C + c] = acc;
             }
         }
+    } else if (valid && C <= 4) {
+        // narrow attributes: one pass over the list, all channels at once
+        float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+        const int32_t* li = vd.index + pix * L;
+        for (int k = 0; k < n; ++k) {
+            const float w = *stg(lane * L + k);
+            const float* ap = vd.attr + (int64_t)li[k] * C;
+            acc0 = fmaf(w, __ldg(ap), acc0);
+            if (C > 1) acc1 = fmaf(w, __ldg(ap + 1), acc1);
+            if (C > 2) acc2 = fmaf(w, __ldg(ap + 2), acc2);
+            if (C > 3) acc3 = fmaf(w, __ldg(ap + 3), acc3);
+        }
+        float* ip = vd.image + pix * C;
+        ip[0] = acc0;
+        if (C > 1) ip[1] = acc1;
+        if (C > 2) ip[2] = acc2;
+        if (C > 3) ip[3] = acc3;
     } else if (valid) {
         // this lane's list: indices from the index output, weights from the staging area
         const bool v4 = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(vd.attr) |
