@@ -26,7 +26,7 @@ constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const Trace& t, const float4& r3, float px,
                                                 float py, float invF, float dqt, float dl, float db, float out[9]) {
     const float4 s0 = __ldg(a.ws.rec2 + 2 * o), s1 = __ldg(a.ws.rec2 + 2 * o + 1);
-    const float ib = 1.0f / t.b;
+    const float ib = rcp_approx(t.b);
     const float Mz = r3.y;
     const float dlt = -Mz * t.num * ib;  // l - Mz
     const float dx = t.du * invF, dy = t.dv * invF;
@@ -95,6 +95,8 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         }
     }
     __syncwarp();
+    // a warp whose 32 lists are all empty has nothing to add
+    if (!__any_sync(0xffffffffu, valid && *stg(lane * L) >= 0)) return;
     // Kept entries occupy slots [KM - K, KM - K + n); slot s holds list
     // position k = s - (KM - K).  The indices live in registers only while
     // the entries are set up; later stages reload them from the list (the
@@ -213,31 +215,40 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         }
         jst[e * NT + tid] = make_float4(acc_dm, -acc_s * J.z, acc_dr, 0.0f);
     }
-    // chain rule to camera space
-    const float inv2tau = 0.5f / tau;
+    // the chain rule reads each entry's results from the stream: .y gets the
+    // k-side sum dl, .w the k-side dA
     {
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
             if (kept(s)) {
-                const float4 J = jst[e * NT + tid];
-                float4 r0, r1, r2, r3;
-                const int64_t o = vb + __ldg(li + (s - (KM - K)));
-                load_rec(a.ws.rec, o, r0, r1, r2, r3);
-                const Trace tr = trace_px(r0, r1, r2, r3, px, py);
-                const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
-                const float er = sqrtf(0.5f * tr.b);
-                const float dqt = fmaf(dA[s], inv2tau, -0.25f * ea * J.x);
-                const float db = J.z / (4.0f * er);
-                float gv[9];
-                chain_to_camera(a, o, tr, r3, px, py, invF, dqt, dl[s] + J.y, db, gv);
-                float* gc = a.ws.gcam + kGcamStride * o;
-                red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
-                red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
-                red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+                float4 J = jst[e * NT + tid];
+                J.y += dl[s];
+                J.w = dA[s];
+                jst[e * NT + tid] = J;
                 ++e;
             }
         }
+    }
+    // chain rule to camera space: a run-time loop over the entries, so that
+    // it holds no per-slot registers
+    const float inv2tau = 0.5f / tau;
+    for (int e = 0; e < n; ++e) {
+        const float4 J = jst[e * NT + tid];
+        float4 r0, r1, r2, r3;
+        const int64_t o = vb + __ldg(li + e);
+        load_rec(a.ws.rec, o, r0, r1, r2, r3);
+        const Trace tr = trace_px(r0, r1, r2, r3, px, py);
+        const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
+        const float er = sqrt_approx(0.5f * tr.b);
+        const float dqt = fmaf(J.w, inv2tau, -0.25f * ea * J.x);
+        const float db = J.z * rcp_approx(4.0f * er);
+        float gv[9];
+        chain_to_camera(a, o, tr, r3, px, py, invF, dqt, J.y, db, gv);
+        float* gc = a.ws.gcam + kGcamStride * o;
+        red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
+        red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
+        red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
     }
 }
 
