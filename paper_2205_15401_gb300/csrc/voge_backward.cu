@@ -52,11 +52,27 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const 
     out[8] = fmaf(dqt, V2 * V2, fmaf(lb, V2, db));
 }
 
-template <int KM, int TH, bool COOP>
+// How a tile adds the attribute gradient dL/dc_g += W_k dL/dI:
+//   kAttrLane:  one reduction per lane and channel (4 <= C < 8),
+//   kAttrWarp:  warp-cooperative rows, lanes over (source pixel, channel) (C >= 8),
+//   kAttrChain: C <= 3, W_k kept in shared memory and added with the third
+//               camera-space vector reduction of the chain rule (slots 9..11
+//               of the record's 12 floats, free otherwise), folded into
+//               grad_attr by the finalize kernel,
+//   kAttrSlot:  C <= 3 for classes without room for W_k in shared memory: the
+//               same slots, with one vector reduction of their own.
+constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3;
+
+// Classes whose W_k buffer fits next to the stream without losing a block per SM.
+template <int KM, int TH>
+__host__ __device__ constexpr bool wk_in_smem() { return TH == 16 && KM <= 20; }
+
+template <int KM, int TH, int AM>
 __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     float4* jst = smem;  // [KM][NT]
+    float* swk = reinterpret_cast<float*>(jst + KM * NT);  // [KM][NT] W_k (kAttrChain)
 
     const int v = view_of_tile(a.views, a.hdr->nviews, t);
     const ViewDesc& vd = a.views[v];
@@ -145,15 +161,10 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
         }
     }
-    // T, W, dA and the attribute gradient dL/dc_g += W_k dL/dI.  With
-    // C >= 8 the attribute gradient is scattered warp-cooperatively: for one
-    // list slot the lanes cover (source lane, channel) pairs, so one
-    // reduction instruction updates whole rows of grad_attr instead of 32
-    // scattered words per channel.  Narrow attributes (C < 8) keep one
-    // reduction per lane and channel, which issues fewer instructions.
+    // T, W, dA and the attribute gradient (see kAttr*)
     const float ntl = -tau * kLog2e;
     const float* gp = vd.grad_image + pix * C;
-    constexpr bool coop = COOP;
+    constexpr bool coop = AM == kAttrWarp;
     const int spi = C <= 32 ? 32 / C : 1;  // source lanes per step
     const int sub = C <= 32 ? lane / C : 0;
     const int cc = C <= 32 ? lane - sub * C : lane;
@@ -172,9 +183,14 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
                 for (int c = 0; c < C; ++c) {
                     const float gc = __ldg(gp + c);
                     G = fmaf(gc, __ldg(ck + c), G);
-                    if (grad_attr && !coop) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
+                    if (AM == kAttrLane && grad_attr) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
                 }
                 dA[s] = -tau * G * Wk;
+                if (AM == kAttrChain) swk[e * NT + tid] = Wk;
+                if (AM == kAttrSlot) {
+                    const float g0 = __ldg(gp), g1 = C > 1 ? __ldg(gp + 1) : 0.0f, g2 = C > 2 ? __ldg(gp + 2) : 0.0f;
+                    red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * g0, Wk * g1, Wk * g2);
+                }
                 ++e;
             }
             if (grad_attr && coop) {
@@ -233,6 +249,12 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     // chain rule to camera space: a run-time loop over the entries, so that
     // it holds no per-slot registers
     const float inv2tau = 0.5f / tau;
+    float gi0 = 0.0f, gi1 = 0.0f, gi2 = 0.0f;  // dL/dI of this pixel (kAttrChain)
+    if (AM == kAttrChain) {
+        gi0 = __ldg(gp);
+        if (C > 1) gi1 = __ldg(gp + 1);
+        if (C > 2) gi2 = __ldg(gp + 2);
+    }
     for (int e = 0; e < n; ++e) {
         const float4 J = jst[e * NT + tid];
         float4 r0, r1, r2, r3;
@@ -248,7 +270,12 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         float* gc = a.ws.gcam + kGcamStride * o;
         red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
         red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
-        red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+        if (AM == kAttrChain) {
+            const float wk = swk[e * NT + tid];
+            red_add_v4(gc + 8, gv[8], wk * gi0, wk * gi1, wk * gi2);
+        } else {
+            red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+        }
     }
 }
 
@@ -258,9 +285,11 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
     for (;;) {
         const int t = next_tile(a, 0, &s_slot);
         if (t < 0) return;
-        // wide attributes take the warp-cooperative attribute scatter
-        if (a.views[view_of_tile(a.views, a.hdr->nviews, t)].C >= 8) backward_tile<KM, TH, true>(a, t);
-        else backward_tile<KM, TH, false>(a, t);
+        const int C = a.views[view_of_tile(a.views, a.hdr->nviews, t)].C;
+        if (C >= 8) backward_tile<KM, TH, kAttrWarp>(a, t);
+        else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t);
+        else if constexpr (wk_in_smem<KM, TH>()) backward_tile<KM, TH, kAttrChain>(a, t);
+        else backward_tile<KM, TH, kAttrSlot>(a, t);
     }
 }
 
@@ -384,8 +413,10 @@ __global__ void __launch_bounds__(256) k_grad_finalize(Args a) {
             float* gc = a.ws.gcam + kGcamStride * t;
             const float dM[3] = {gc[0], gc[1], gc[2]};
             const float G[9] = {gc[3], gc[4], gc[5], gc[4], gc[6], gc[7], gc[5], gc[7], gc[8]};
+            if (vd.C <= 3 && vd.grad_attr)  // narrow attribute gradients ride in slots 9..11
+                for (int c = 0; c < vd.C; ++c) atomicAdd(vd.grad_attr + (int64_t)vd.C * g + c, gc[9 + c]);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) gc[q] = 0.0f;
+            for (int q = 0; q < 12; ++q) gc[q] = 0.0f;
             float R[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) R[q] = vd.R[q];
@@ -473,7 +504,7 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
 
 template <int KM, int TH>
 static size_t backward_smem_bytes() {
-    return (size_t)KM * 16 * TH * 16;
+    return (size_t)KM * 16 * TH * (wk_in_smem<KM, TH>() ? 20 : 16);
 }
 
 template <typename Kern>
@@ -519,7 +550,7 @@ __global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
     for (int gb = blockIdx.x * blockDim.x; gb < N; gb += gridDim.x * blockDim.x) {
         const int g = gb + threadIdx.x;
         const bool live = g < N;
-        float gm[3] = {0.f, 0.f, 0.f}, gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float gm[3] = {0.f, 0.f, 0.f}, gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, ga[3] = {0.f, 0.f, 0.f};
         float Mw[3] = {0.f, 0.f, 0.f}, Pw[9];
         const ViewDesc& v0 = a.views[0];
         if (live) {
@@ -543,7 +574,8 @@ __global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
                 G[0] = gc[3]; G[1] = gc[4]; G[2] = gc[5];
                 G[3] = gc[4]; G[4] = gc[6]; G[5] = gc[7];
                 G[6] = gc[5]; G[7] = gc[7]; G[8] = gc[8];
-                for (int q = 0; q < 9; ++q) gc[q] = 0.0f;
+                ga[0] += gc[9]; ga[1] += gc[10]; ga[2] += gc[11];  // narrow attribute gradients
+                for (int q = 0; q < 12; ++q) gc[q] = 0.0f;
             }
             for (int q = 0; q < 3; ++q) gm[q] += R[q] * dM[0] + R[3 + q] * dM[1] + R[6 + q] * dM[2];
             float GR[9];
@@ -584,6 +616,8 @@ __global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
             for (int q = 0; q < 3; ++q) v0.grad_means[3 * (int64_t)g + q] += gm[q];
         if (v0.grad_inv_cov)
             for (int q = 0; q < 6; ++q) v0.grad_inv_cov[6 * (int64_t)g + q] += gw[q];
+        if (v0.C <= 3 && v0.grad_attr)
+            for (int c = 0; c < v0.C; ++c) v0.grad_attr[(int64_t)v0.C * g + c] += ga[c];
     }
 }
 

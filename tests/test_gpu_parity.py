@@ -212,13 +212,30 @@ def test_nearly_flat_gaussians():
 
 
 # ------------------------------------------------------------ gradients ---
-@pytest.mark.parametrize("K,eta", [(8, 0.01), (20, 0.001), (0, 0.0)])
+@pytest.mark.parametrize("K,eta", [(8, 0.01), (20, 0.001), (24, 0.001), (32, 0.01), (0, 0.0)])
 def test_backward_small_scene(K, eta):
     sc = scenes.fit_8x512(seed=11, N=500, B=2, side=40)
     cams, m, p, a = scene_inputs(sc)
     p = p / 16.0  # wider kernels at this small size
     r, dev, img, w, idx = gpu_forward(cams, m, p, a, K, 1.0, eta)
     g = np.random.default_rng(12).standard_normal(img.shape)
+    got = gpu_backward(r, dev, idx, g)
+    want = oracle.render_bwd(cams, m, p, a, 1.0, oracle.all_pixels(cams), idx, g)
+    for k in ("g_means", "g_inv_cov", "g_attr", "g_R", "g_T"):
+        assert rel_err(got[k], want[k]) <= TOL_GRAD, (k, rel_err(got[k], want[k]))
+
+
+@pytest.mark.parametrize("C", [1, 2, 3, 5, 8, 16])
+@pytest.mark.parametrize("K", [16, 32])
+def test_backward_attribute_widths(C, K):
+    """Every way the attribute gradient is gathered (slots of the camera-space
+    sums for C <= 3, one reduction per channel, warp rows for C >= 8) in a
+    class with and one without the shared-memory W buffer."""
+    sc = scenes.fit_8x512(seed=40 + C, N=400, B=2, side=36, C=C)
+    cams, m, p, a = scene_inputs(sc)
+    p = p / 16.0
+    r, dev, img, w, idx = gpu_forward(cams, m, p, a, K, 1.0, 0.005)
+    g = np.random.default_rng(41).standard_normal(img.shape)
     got = gpu_backward(r, dev, idx, g)
     want = oracle.render_bwd(cams, m, p, a, 1.0, oracle.all_pixels(cams), idx, g)
     for k in ("g_means", "g_inv_cov", "g_attr", "g_R", "g_T"):
