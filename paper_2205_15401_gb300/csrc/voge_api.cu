@@ -14,7 +14,7 @@ namespace voge {
 cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
-cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a);
+cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int render_blocks_per_sm(int KM);
 int backward_blocks_per_sm(int KM);
 
@@ -67,7 +67,7 @@ void pick_variant(int L, int* KM, int* TH) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t desc, rec, rec2, tbox, tile_cnt, tile_off, tile_cur, tile_gauss, gcam, gkey, gid, total;
+    size_t desc, rec, rec2, tbox, tile_cnt, tile_off, tile_sub, tile_gauss, gcam, gkey, gid, total;
     int64_t pixels, bin_cap;
     int32_t total_tiles, TH, KM, L;
 };
@@ -111,7 +111,7 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.tbox = o; o = align256(o + 16 * (size_t)BN);
     l.tile_cnt = o; o = align256(o + 4 * (size_t)(tiles + 1));
     l.tile_off = o; o = align256(o + 4 * (size_t)(tiles + 1));
-    l.tile_cur = o; o = align256(o + 4 * (size_t)(tiles + 1));
+    l.tile_sub = o; o = align256(o + 4 * (size_t)kTileSub * (size_t)(tiles + 1));
     l.tile_gauss = o; o = align256(o + 4 * (size_t)l.bin_cap);
     l.gcam = o; o = align256(o + 4 * kGcamStride * (size_t)BN);
     if (l.KM == 0 && l.L > 0) {
@@ -132,7 +132,7 @@ Ws make_ws(const Layout& l, void* base) {
     w.tbox = reinterpret_cast<int4*>(b + l.tbox);
     w.tile_cnt = reinterpret_cast<int32_t*>(b + l.tile_cnt);
     w.tile_off = reinterpret_cast<int32_t*>(b + l.tile_off);
-    w.tile_cur = reinterpret_cast<int32_t*>(b + l.tile_cur);
+    w.tile_sub = reinterpret_cast<int32_t*>(b + l.tile_sub);
     w.tile_gauss = reinterpret_cast<int32_t*>(b + l.tile_gauss);
     w.bin_cap = l.bin_cap;
     w.gcam = reinterpret_cast<float*>(b + l.gcam);
@@ -237,7 +237,7 @@ int upload_and_project(const voge_camera* cams, const voge_params* p, const Layo
         return VOGE_ERR_CUDA;
     if (!project) return VOGE_OK;
     const int count_tiles = bin && !(p->flags & VOGE_FLAG_PLAIN);
-    if (count_tiles && cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(l.total_tiles + 1), s) != cudaSuccess)
+    if (count_tiles && cudaMemsetAsync(a.ws.tile_sub, 0, 4 * (size_t)kTileSub * (size_t)(l.total_tiles + 1), s) != cudaSuccess)
         return VOGE_ERR_CUDA;
     return launch_project(record_grid((int64_t)p->B * p->N), l.total_tiles, count_tiles, s, a) == cudaSuccess ? VOGE_OK
                                                                                                 : VOGE_ERR_CUDA;
@@ -390,7 +390,7 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
     if (l.total_tiles > 0 && launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
     if ((grad_means || grad_inv_cov || grad_cam) &&
-        launch_grad_finalize(record_grid(p->N), 1, s, a) != cudaSuccess)
+        launch_grad_finalize(record_grid(p->N), p->B, p->N, 1, s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
     return VOGE_OK;
 }

@@ -539,92 +539,123 @@ cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Arg
     }
 }
 
-// Shared-scene form (every view renders the same N Gaussians): one thread
-// per Gaussian loops over the views, so world gradients are written once
-// without atomics, and the pose sums are reduced per block.
-__global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
+// Shared-scene form (every view renders the same N Gaussians), in two
+// kernels.  k_pose_grad_shared: one thread per (view, Gaussian) turns the
+// camera-space sums into that view's pose gradient (Sec. 3.3 chain through
+// M = R M_w + T, P = R P_w R^T), reduced per block.  k_grad_finalize_shared:
+// one thread per Gaussian rotates the sums of every view into world space and
+// adds them up, so world gradients are written once without atomics; it also
+// clears the sums for the next call.
+__global__ void __launch_bounds__(256) k_pose_grad_shared(Args a) {
     __shared__ float red[8][12];
-    const int nv = a.hdr->nviews;
-    const int N = a.views[0].N;
+    const int v = blockIdx.y;
+    const ViewDesc& vd = a.views[v];
+    if (!vd.grad_cam) return;  // uniform in the block
+    const int N = vd.N;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int gb = blockIdx.x * blockDim.x; gb < N; gb += gridDim.x * blockDim.x) {
-        const int g = gb + threadIdx.x;
-        const bool live = g < N;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    float p[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) p[q] = 0.0f;
+    if (g < N) {
+        const float4* gc4 = reinterpret_cast<const float4*>(a.ws.gcam + kGcamStride * (vd.rec_base + g));
+        const float4 c0 = gc4[0], c1 = gc4[1], c2 = gc4[2];
+        const float dM[3] = {c0.x, c0.y, c0.z};
+        const float G[9] = {c0.w, c1.x, c1.y, c1.x, c1.z, c1.w, c1.y, c1.w, c2.x};
+        float R[9], Mw[3], Pw[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) R[q] = vd.R[q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Mw[q] = __ldg(vd.means + 3 * (int64_t)g + q);
+        const float* p6 = vd.inv_cov + 6 * (int64_t)g;
+        Pw[0] = __ldg(p6 + 0); Pw[1] = __ldg(p6 + 1); Pw[2] = __ldg(p6 + 2);
+        Pw[3] = Pw[1]; Pw[4] = __ldg(p6 + 3); Pw[5] = __ldg(p6 + 4);
+        Pw[6] = Pw[2]; Pw[7] = Pw[5]; Pw[8] = __ldg(p6 + 5);
+        float RP[9];
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int y = 0; y < 3; ++y) RP[3 * x + y] = R[3 * x] * Pw[y] + R[3 * x + 1] * Pw[3 + y] + R[3 * x + 2] * Pw[6 + y];
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int y = 0; y < 3; ++y)
+                p[3 * x + y] = dM[x] * Mw[y] + 2.0f * (G[3 * x] * RP[y] + G[3 * x + 1] * RP[3 + y] + G[3 * x + 2] * RP[6 + y]);
+        p[9] = dM[0];
+        p[10] = dM[1];
+        p[11] = dM[2];
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        float x = p[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        float sum = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+        atomicAdd(vd.grad_cam + threadIdx.x, sum);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grad_finalize_shared(Args a) {
+    const int nv = a.hdr->nviews;
+    const ViewDesc& v0 = a.views[0];
+    const int N = v0.N, C = v0.C;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
         float gm[3] = {0.f, 0.f, 0.f}, gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, ga[3] = {0.f, 0.f, 0.f};
-        float Mw[3] = {0.f, 0.f, 0.f}, Pw[9];
-        const ViewDesc& v0 = a.views[0];
-        if (live) {
-            for (int q = 0; q < 3; ++q) Mw[q] = __ldg(v0.means + 3 * (int64_t)g + q);
-            const float* p6 = v0.inv_cov + 6 * (int64_t)g;
-            Pw[0] = __ldg(p6 + 0); Pw[1] = __ldg(p6 + 1); Pw[2] = __ldg(p6 + 2);
-            Pw[3] = Pw[1]; Pw[4] = __ldg(p6 + 3); Pw[5] = __ldg(p6 + 4);
-            Pw[6] = Pw[2]; Pw[7] = Pw[5]; Pw[8] = __ldg(p6 + 5);
-        } else {
-            for (int q = 0; q < 9; ++q) Pw[q] = 0.0f;
-        }
         for (int v = 0; v < nv; ++v) {
             const ViewDesc& vd = a.views[v];
+            float4* gc4 = reinterpret_cast<float4*>(a.ws.gcam + kGcamStride * (vd.rec_base + g));
+            const float4 c0 = gc4[0], c1 = gc4[1], c2 = gc4[2];
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            gc4[0] = z;
+            gc4[1] = z;
+            gc4[2] = z;
             float R[9];
+#pragma unroll
             for (int q = 0; q < 9; ++q) R[q] = vd.R[q];
-            float dM[3] = {0.f, 0.f, 0.f}, G[9];
-            for (int q = 0; q < 9; ++q) G[q] = 0.0f;
-            if (live) {
-                float* gc = a.ws.gcam + kGcamStride * (vd.rec_base + g);
-                dM[0] = gc[0]; dM[1] = gc[1]; dM[2] = gc[2];
-                G[0] = gc[3]; G[1] = gc[4]; G[2] = gc[5];
-                G[3] = gc[4]; G[4] = gc[6]; G[5] = gc[7];
-                G[6] = gc[5]; G[7] = gc[7]; G[8] = gc[8];
-                ga[0] += gc[9]; ga[1] += gc[10]; ga[2] += gc[11];  // narrow attribute gradients
-                for (int q = 0; q < 12; ++q) gc[q] = 0.0f;
-            }
+            const float dM[3] = {c0.x, c0.y, c0.z};
+            const float G[9] = {c0.w, c1.x, c1.y, c1.x, c1.z, c1.w, c1.y, c1.w, c2.x};
+            ga[0] += c2.y;  // narrow attribute gradients (slots 9..11)
+            ga[1] += c2.z;
+            ga[2] += c2.w;
+#pragma unroll
             for (int q = 0; q < 3; ++q) gm[q] += R[q] * dM[0] + R[3 + q] * dM[1] + R[6 + q] * dM[2];
             float GR[9];
+#pragma unroll
             for (int x = 0; x < 3; ++x)
+#pragma unroll
                 for (int y = 0; y < 3; ++y) GR[3 * x + y] = G[3 * x] * R[y] + G[3 * x + 1] * R[3 + y] + G[3 * x + 2] * R[6 + y];
             float Gw[9];
+#pragma unroll
             for (int x = 0; x < 3; ++x)
+#pragma unroll
                 for (int y = 0; y < 3; ++y) Gw[3 * x + y] = R[x] * GR[y] + R[3 + x] * GR[3 + y] + R[6 + x] * GR[6 + y];
             gw[0] += Gw[0]; gw[1] += Gw[1] + Gw[3]; gw[2] += Gw[2] + Gw[6];
             gw[3] += Gw[4]; gw[4] += Gw[5] + Gw[7]; gw[5] += Gw[8];
-            if (vd.grad_cam) {
-                float RP[9];
-                for (int x = 0; x < 3; ++x)
-                    for (int y = 0; y < 3; ++y) RP[3 * x + y] = R[3 * x] * Pw[y] + R[3 * x + 1] * Pw[3 + y] + R[3 * x + 2] * Pw[6 + y];
-                float p[12];
-                for (int x = 0; x < 3; ++x)
-                    for (int y = 0; y < 3; ++y)
-                        p[3 * x + y] = dM[x] * Mw[y] + 2.0f * (G[3 * x] * RP[y] + G[3 * x + 1] * RP[3 + y] + G[3 * x + 2] * RP[6 + y]);
-                p[9] = dM[0]; p[10] = dM[1]; p[11] = dM[2];
-                for (int q = 0; q < 12; ++q) {
-                    float x = p[q];
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    p[q] = x;
-                }
-                if (lane == 0)
-                    for (int q = 0; q < 12; ++q) red[wid][q] = p[q];
-                __syncthreads();
-                if (threadIdx.x < 12) {
-                    float sum = 0.0f;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
-                    atomicAdd(vd.grad_cam + threadIdx.x, sum);
-                }
-                __syncthreads();
-            }
         }
-        if (!live) continue;
         if (v0.grad_means)
             for (int q = 0; q < 3; ++q) v0.grad_means[3 * (int64_t)g + q] += gm[q];
         if (v0.grad_inv_cov)
             for (int q = 0; q < 6; ++q) v0.grad_inv_cov[6 * (int64_t)g + q] += gw[q];
-        if (v0.C <= 3 && v0.grad_attr)
-            for (int c = 0; c < v0.C; ++c) v0.grad_attr[(int64_t)v0.C * g + c] += ga[c];
+        if (C <= 3 && v0.grad_attr)
+            for (int c = 0; c < C; ++c) v0.grad_attr[(int64_t)C * g + c] += ga[c];
     }
 }
 
-cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a) {
+cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a) {
     TraceScope tr("k_grad_finalize", s);
-    if (shared_scene) k_grad_finalize_shared<<<grid, 256, 0, s>>>(a);
-    else k_grad_finalize<<<grid, 256, 0, s>>>(a);
+    if (shared_scene) {
+        if (N > 0 && nviews > 0) {
+            k_pose_grad_shared<<<dim3((N + 255) / 256, nviews), 256, 0, s>>>(a);
+            k_grad_finalize_shared<<<grid, 256, 0, s>>>(a);
+        }
+    } else {
+        k_grad_finalize<<<grid, 256, 0, s>>>(a);
+    }
     return cudaPeekAtLastError();
 }
 

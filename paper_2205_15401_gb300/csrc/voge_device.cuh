@@ -30,6 +30,7 @@ namespace voge {
 
 constexpr int kTileW = 16;     // tile width in pixels (one warp covers 16 x 2 pixels)
 constexpr int kSortMax = 2048; // tiles with more candidates are processed unsorted
+constexpr int kTileSub = 8;    // counters per tile for binning (spreads same-address atomics)
 constexpr float kLog2e = 1.4426950408889634f;
 
 // One view as the kernels read it: the camera, the scene this view renders
@@ -359,12 +360,12 @@ struct Ws {
     float4* rec;      // [records][4]
     float4* rec2;     // [records][2]
     int4* tbox;       // [records]: tile range tx0, tx1, ty0, ty1 (tx0 > tx1: none)
-    int32_t* tile_cnt;
-    int32_t* tile_off;
-    int32_t* tile_cur;
+    int32_t* tile_cnt;  // [tiles] candidates per tile (written by the scan)
+    int32_t* tile_off;  // [tiles] first list entry of each tile
+    int32_t* tile_sub;  // [tiles][kTileSub] counts per sub-counter, then scatter cursors
     int32_t* tile_gauss;
     int64_t bin_cap;
-    float* gcam;      // [records][12] backward accumulators: dM (3), G (6), zero padding (3)
+    float* gcam;      // [records][12] backward accumulators: dM (3), G (6), narrow attribute gradient (3)
     float* gkey;      // generic-path per-pixel scratch
     int32_t* gid;
     int32_t gen_L;    // list length the generic scratch is laid out for

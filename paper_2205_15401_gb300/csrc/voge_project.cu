@@ -149,8 +149,12 @@ __device__ __forceinline__ void project_one(const Args& a, int v, int64_t t, int
     a.ws.rec2[2 * t + 1] = s1;
     a.ws.tbox[t] = tb;
     if (count_tiles && !plain) {
+        // one of kTileSub counters per tile, picked by the Gaussian index, so
+        // that the many Gaussians of a busy tile do not all hit one address
+        const int sub = g & (kTileSub - 1);
         for (int ty = tb.z; ty <= tb.w; ++ty)
-            for (int tx = tb.x; tx <= tb.y; ++tx) atomicAdd(&a.ws.tile_cnt[tile_base + ty * tiles_x + tx], 1);
+            for (int tx = tb.x; tx <= tb.y; ++tx)
+                atomicAdd(&a.ws.tile_sub[(tile_base + ty * tiles_x + tx) * kTileSub + sub], 1);
     }
 }
 
@@ -162,8 +166,10 @@ __global__ void __launch_bounds__(256) k_project(Args a, int count_tiles) {
     }
 }
 
-// Exclusive scan of the per-tile counts (one CTA of 1024 threads; each thread
-// owns a contiguous run).  Also seeds the scatter cursors.
+// Exclusive scan of the per-(tile, sub-counter) counts in tile order (one CTA
+// of 1024 threads; each thread owns a contiguous run of tiles).  Writes each
+// tile's count and first entry, and turns the sub-counts into the scatter
+// cursors (a tile's list is its sub-lists back to back).
 __global__ void __launch_bounds__(1024) k_scan_tiles(Args a) {
     __shared__ int32_t warp_sums[32];
     const Ws& ws = a.ws;
@@ -172,7 +178,9 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Args a) {
     const int per = (n + 1023) / 1024;
     const int beg = min(n, tid * per), end = min(n, beg + per);
     int32_t s = 0;
-    for (int q = beg; q < end; ++q) s += ws.tile_cnt[q];
+    for (int q = beg; q < end; ++q)
+#pragma unroll
+        for (int u = 0; u < kTileSub; ++u) s += ws.tile_sub[q * kTileSub + u];
     // block exclusive scan of s
     int32_t x = s;
     const int lane = tid & 31, wid = tid >> 5;
@@ -196,8 +204,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Args a) {
     int32_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0);
     for (int q = beg; q < end; ++q) {
         ws.tile_off[q] = run;
-        ws.tile_cur[q] = run;
-        run += ws.tile_cnt[q];
+        const int32_t first = run;
+#pragma unroll
+        for (int u = 0; u < kTileSub; ++u) {
+            const int32_t c = ws.tile_sub[q * kTileSub + u];
+            ws.tile_sub[q * kTileSub + u] = run;
+            run += c;
+        }
+        ws.tile_cnt[q] = run - first;
     }
 }
 
@@ -211,9 +225,10 @@ __global__ void __launch_bounds__(256) k_scatter(Args a) {
         if (__ldg(&a.views[v].plain)) continue;
         const int g = (int)(t - __ldg(&a.views[v].rec_base));
         const int tiles_x = __ldg(&a.views[v].tiles_x), tile_base = __ldg(&a.views[v].tile_base);
+        const int sub = g & (kTileSub - 1);
         for (int ty = tb.z; ty <= tb.w; ++ty)
             for (int tx = tb.x; tx <= tb.y; ++tx) {
-                const int pos = atomicAdd(&a.ws.tile_cur[tile_base + ty * tiles_x + tx], 1);
+                const int pos = atomicAdd(&a.ws.tile_sub[(tile_base + ty * tiles_x + tx) * kTileSub + sub], 1);
                 if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
             }
     }

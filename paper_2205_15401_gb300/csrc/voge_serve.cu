@@ -33,7 +33,7 @@ namespace voge {
 cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
-cudaError_t launch_grad_finalize(int grid, int shared_scene, cudaStream_t s, const Args& a);
+cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int tile_grid(int KM, int fwd, int total_tiles);
 
 // Loss helper over a batch: per view, grad_image = 2 (image - target) / n and
@@ -183,7 +183,7 @@ struct voge_server {
     int64_t max_records = 0, max_tiles = 0, max_elems = 0;
     int max_views = 0;
     int grid_records = 0;
-    size_t ws_rec = 0, ws_rec2 = 0, ws_tbox = 0, ws_cnt = 0, ws_off = 0, ws_cur = 0, ws_gauss = 0, ws_gcam = 0;
+    size_t ws_rec = 0, ws_rec2 = 0, ws_tbox = 0, ws_cnt = 0, ws_off = 0, ws_sub = 0, ws_gauss = 0, ws_gcam = 0;
     int64_t bin_cap = 0;
     size_t request_capacity = 0;  // arena bytes left for requests
 
@@ -339,7 +339,7 @@ cudaError_t issue_tick(voge_server* S, TickSlot& ts, uint32_t mask) {
     const Args& a = ts.args;
     cudaError_t e = cudaMemcpyAsync(a.hdr, ts.host_desc, ts.desc_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.ws.tile_cnt, 0, 4 * (size_t)(S->max_tiles + 1), s);
+    e = cudaMemsetAsync(a.ws.tile_sub, 0, 4 * (size_t)kTileSub * (size_t)(S->max_tiles + 1), s);
     if (e != cudaSuccess) return e;
     e = launch_project(S->grid_records, (int)std::min<int64_t>(S->max_tiles, (int64_t)S->grid_records * 8), 1, s, a);
     if (e != cudaSuccess) return e;
@@ -360,7 +360,7 @@ cudaError_t issue_tick(voge_server* S, TickSlot& ts, uint32_t mask) {
         e = launch_backward_tiles(kClassKM[c], tile_grid(kClassKM[c], 0, 1 << 30), s, ac);
         if (e != cudaSuccess) return e;
     }
-    return launch_grad_finalize(S->grid_records, 0, s, a);
+    return launch_grad_finalize(S->grid_records, 0, 0, 0, s, a);
 }
 
 int run_tick(voge_server* S, TickSlot& ts) {
@@ -562,7 +562,7 @@ int voge_server_create(const voge_server_config* cfg, voge_server** out) {
     S->ws_tbox = o; o += up256(16 * (size_t)S->max_records);
     S->ws_cnt = o; o += up256(4 * (size_t)(S->max_tiles + 1));
     S->ws_off = o; o += up256(4 * (size_t)(S->max_tiles + 1));
-    S->ws_cur = o; o += up256(4 * (size_t)(S->max_tiles + 1));
+    S->ws_sub = o; o += up256(4 * (size_t)kTileSub * (size_t)(S->max_tiles + 1));
     S->ws_gauss = o; o += up256(4 * (size_t)S->bin_cap);
     S->ws_gcam = o; o += up256(4 * kGcamStride * (size_t)S->max_records);
     const size_t tick_bytes = o;
@@ -596,7 +596,7 @@ int voge_server_create(const voge_server_config* cfg, voge_server** out) {
         a.ws.tbox = reinterpret_cast<int4*>(b + S->ws_tbox);
         a.ws.tile_cnt = reinterpret_cast<int32_t*>(b + S->ws_cnt);
         a.ws.tile_off = reinterpret_cast<int32_t*>(b + S->ws_off);
-        a.ws.tile_cur = reinterpret_cast<int32_t*>(b + S->ws_cur);
+        a.ws.tile_sub = reinterpret_cast<int32_t*>(b + S->ws_sub);
         a.ws.tile_gauss = reinterpret_cast<int32_t*>(b + S->ws_gauss);
         a.ws.bin_cap = S->bin_cap;
         a.ws.gcam = reinterpret_cast<float*>(b + S->ws_gcam);
