@@ -38,11 +38,13 @@ WORKLOAD = dict(views=8, side=512, N=50_000, K=20, eta=0.01, C=3, tau=1.0)
 #   forward  24 = depth difference of two-float l (3) + scale (1) + A&S 7.1.28
 #             erf: degree-6 polynomial (12) + 4 squarings (4) + reciprocal (1)
 #             + signed accumulation (3)
-#   backward 52 = the forward pair recomputed (24) + adjoint pair: difference
-#             and scale (4), A&S 7.1.26 erf with e^{-u^2} (15), accumulation of
-#             dm, du, dl_k, dl_j, dr (9)
+#   backward 28 = adjoint pair: difference and scale (4), A&S 7.1.26 erf with
+#             e^{-u^2} (15), accumulation of dm, du, dl_k, dl_j, dr (9); the
+#             timed step hands the forward's weights to the backward
+#             (voge_render_bwd_w), so the forward pair is not recomputed
+#             (it would add 24)
 # plus, per kept entry, 80 FLOP for the chain to camera space (backward only).
-FLOP_PER_PAIR = {"fwd": 24, "bwd": 52}
+FLOP_PER_PAIR = {"fwd": 24, "bwd": 28}
 FLOP_PER_ENTRY_BWD = 80
 # GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -363,7 +365,8 @@ def main():
         r.forward(means, inv_cov, attr, out=(image, weights, index))
         loss.zero_()
         voge.voge_mse_grad(image, target, g_image, loss)
-        r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam, reuse_projection=True)
+        r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam, reuse_projection=True,
+                   weights=weights)
         step_no[0] += 1
         voge.voge_adam_step(par, grad, m_adam, v_adam, lr=1e-4, step=step_no[0])
 
@@ -439,7 +442,7 @@ def main():
             grad.zero_()
             g_cam.zero_()
             r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam,
-                       reuse_projection=True)
+                       reuse_projection=True, weights=weights)
             h_grad.copy_(grad, non_blocking=True)
             h_gcam.copy_(g_cam, non_blocking=True)
             h_loss.copy_(loss, non_blocking=True)
@@ -470,7 +473,7 @@ def main():
             loss.zero_()
             voge.voge_mse_grad(image, target, g_image, loss)
             rp.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam,
-                        reuse_projection=True)
+                        reuse_projection=True, weights=weights)
             grad.zero_()
 
         plain_step()

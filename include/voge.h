@@ -150,6 +150,23 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
                     size_t workspace_bytes, voge_stream_t stream);
 
 /*
+ * voge_render_bwd with the forward's weights supplied.  W_k = T(l_k) e^{q_k}
+ * of Eq. 7 is the only quantity of the backward pass that needs the
+ * transmittance sum over the whole list; taking it from the forward pass
+ * removes that recomputation.  Same results as voge_render_bwd up to the
+ * rounding of W (the forward computes it with the same arithmetic).
+ *
+ *   weights  device, [pixels][L] float: the `weights` output of the
+ *            voge_render_fwd call that produced `index` (same cameras,
+ *            parameters and scene), or NULL to recompute W from `index`.
+ *   All other arguments, ownership and errors as voge_render_bwd.
+ */
+int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                      const float* attr, const int32_t* index, const float* weights, const float* grad_image,
+                      float* grad_means, float* grad_inv_cov, float* grad_attr, float* grad_cam, void* workspace,
+                      size_t workspace_bytes, voge_stream_t stream);
+
+/*
  * Camera pose (azimuth, elevation, distance, roll), radians -> R, T (host).
  * Look-at camera: centre dist*(cos e sin a, sin e, cos e cos a), looking at
  * the world origin, world up +y, then a roll about the optical axis.  The

@@ -147,6 +147,7 @@ struct Buffers {
     float *image, *weights;
     int32_t* index;
     const int32_t* index_in;
+    const float* weights_in;
     const float* grad_image;
     float *grad_means, *grad_inv_cov, *grad_attr, *grad_cam;
 };
@@ -193,6 +194,7 @@ void build_views(const voge_camera* cams, const voge_params* p, const Layout& l,
         d.weights = b.weights ? b.weights + pix_base * l.L : nullptr;
         d.index = b.index ? b.index + pix_base * l.L : nullptr;
         d.index_in = b.index_in ? b.index_in + pix_base * l.L : nullptr;
+        d.weights_in = b.weights_in ? b.weights_in + pix_base * l.L : nullptr;
         d.grad_image = b.grad_image ? b.grad_image + pix_base * p->C : nullptr;
         d.grad_means = b.grad_means;
         d.grad_inv_cov = b.grad_inv_cov;
@@ -364,6 +366,14 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
                     const float* attr, const int32_t* index, const float* grad_image, float* grad_means,
                     float* grad_inv_cov, float* grad_attr, float* grad_cam, void* workspace, size_t workspace_bytes,
                     voge_stream_t stream_) {
+    return voge_render_bwd_w(cams, p, means, inv_cov, attr, index, nullptr, grad_image, grad_means, grad_inv_cov,
+                             grad_attr, grad_cam, workspace, workspace_bytes, stream_);
+}
+
+int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                      const float* attr, const int32_t* index, const float* weights, const float* grad_image,
+                      float* grad_means, float* grad_inv_cov, float* grad_attr, float* grad_cam, void* workspace,
+                      size_t workspace_bytes, voge_stream_t stream_) {
     if (!valid_params(cams, p) || !grad_image) return VOGE_ERR_ARG;
     if (p->N == 0) return VOGE_OK;
     if (!means || !inv_cov || !attr || !index) return VOGE_ERR_ARG;
@@ -378,6 +388,7 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
     b.inv_cov = inv_cov;
     b.attr = attr;
     b.index_in = index;
+    b.weights_in = weights;
     b.grad_image = grad_image;
     b.grad_means = grad_means;
     b.grad_inv_cov = grad_inv_cov;
@@ -389,7 +400,8 @@ int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* 
     if (cudaMemsetAsync(a.ws.gcam, 0, 4 * kGcamStride * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
     if (l.total_tiles > 0 && launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
-    if ((grad_means || grad_inv_cov || grad_cam) &&
+    // the finalize also folds in attribute gradients of up to three channels
+    if ((grad_means || grad_inv_cov || grad_cam || grad_attr) &&
         launch_grad_finalize(record_grid(p->N), p->B, p->N, 1, s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
     return VOGE_OK;

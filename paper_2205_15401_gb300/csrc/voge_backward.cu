@@ -147,11 +147,12 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     }
     const int32_t* li = vd.index_in + pix * L;
     auto kept = [&](int s) { return s >= KM - K && s - (KM - K) < n; };
-    // loop 1: A_k
+    // loop 1: A_k (skipped when the forward's W_k are supplied)
+    const float* wi = vd.weights_in ? vd.weights_in + pix * L : nullptr;
     float A[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s) A[s] = 0.0f;
-    for (int e = 0; e < n; ++e) {
+    for (int e = 0; e < (wi ? 0 : n); ++e) {
         const float4 J = jst[e * NT + tid];
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
@@ -177,7 +178,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
             int32_t g = -1;
             if (kept(s)) {
                 g = __ldg(li + (s - (KM - K)));
-                Wk = ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
+                Wk = wi ? __ldg(wi + (s - (KM - K))) : ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
                 const float* ck = attr + (int64_t)g * C;
                 float G = 0.0f;
                 for (int c = 0; c < C; ++c) {

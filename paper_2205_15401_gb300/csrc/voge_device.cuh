@@ -68,6 +68,8 @@ struct ViewDesc {
     float* grad_inv_cov;      // [N][6] or null
     float* grad_attr;         // [N][C] or null
     float* grad_cam;          // [12] or null
+    const float* weights_in;  // [H*W][L] W_k of the forward pass, or null (backward recomputes them)
+    const void* pad4;
 };
 static_assert(sizeof(ViewDesc) % 16 == 0, "ViewDesc layout");
 

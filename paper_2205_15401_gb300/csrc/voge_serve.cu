@@ -312,6 +312,7 @@ uint32_t build_tick(voge_server* S, TickSlot& ts) {
         d.weights = q->weights;
         d.index = q->index;
         d.index_in = q->index;
+        d.weights_in = q->weights;  // the tick's own forward pass wrote them
         d.grad_image = q->grad_image;
         d.target = q->target;
         d.loss = q->loss;

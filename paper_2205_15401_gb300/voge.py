@@ -8,8 +8,8 @@ not been built, or a call fails, a RuntimeError is raised.
 
 On top of the binding sit ``Renderer`` (workspace management) and
 ``VoGERender`` (a ``torch.autograd.Function`` whose forward is
-``voge_render_fwd`` and whose backward is ``voge_render_bwd``; it saves only
-the per-pixel index lists).
+``voge_render_fwd`` and whose backward is ``voge_render_bwd_w``; it saves the
+per-pixel index lists and weights).
 """
 from __future__ import annotations
 
@@ -66,6 +66,9 @@ def lib():
             L.voge_render_bwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                           ctypes.c_size_t, vp]
             L.voge_render_bwd.restype = ctypes.c_int
+            L.voge_render_bwd_w.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                            vp, ctypes.c_size_t, vp]
+            L.voge_render_bwd_w.restype = ctypes.c_int
             L.voge_pose_to_RT.argtypes = [P(ctypes.c_double), P(ctypes.c_float), P(ctypes.c_float)]
             L.voge_pose_to_RT.restype = None
             L.voge_pose_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
@@ -161,6 +164,17 @@ def voge_render_bwd(cams, params, means, inv_cov, attr, index, grad_image, grad_
                                _ptr(grad_inv_cov, f32), _ptr(grad_attr, f32), _ptr(grad_cam, f32),
                                _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "voge_render_bwd")
+
+
+def voge_render_bwd_w(cams, params, means, inv_cov, attr, index, weights, grad_image, grad_means, grad_inv_cov,
+                      grad_attr, grad_cam, workspace, stream=None):
+    """voge_render_bwd taking the forward's weights (or None to recompute them)."""
+    f32, i32 = torch.float32, torch.int32
+    rc = lib().voge_render_bwd_w(cams, ctypes.byref(params), _ptr(means, f32), _ptr(inv_cov, f32), _ptr(attr, f32),
+                                 _ptr(index, i32), _ptr(weights, f32), _ptr(grad_image, f32), _ptr(grad_means, f32),
+                                 _ptr(grad_inv_cov, f32), _ptr(grad_attr, f32), _ptr(grad_cam, f32),
+                                 _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "voge_render_bwd_w")
 
 
 def voge_render_fwd_static(cams, params, means, inv_cov, attr, image, weights, index, stream=None):
@@ -262,13 +276,19 @@ class Renderer:
         return image, weights, index
 
     def backward(self, means, inv_cov, attr, index, grad_image, grad_means=None, grad_inv_cov=None, grad_attr=None,
-                 grad_cam=None, reuse_projection=False):
+                 grad_cam=None, reuse_projection=False, weights=None):
+        """Accumulate gradients.  ``weights``: the forward's weights output for
+        the same ``index`` (skips recomputing W), or None."""
         params = self.params
         if reuse_projection:
             params = make_params(params.B, params.N, params.C, params.K, params.tau, params.thresh,
                                  params.flags | VOGE_FLAG_REUSE_PROJECTION, params.bin_capacity)
-        voge_render_bwd(self.cams, params, means, inv_cov, attr, index, grad_image, grad_means, grad_inv_cov,
-                        grad_attr, grad_cam, self.workspace)
+        if weights is None:
+            voge_render_bwd(self.cams, params, means, inv_cov, attr, index, grad_image, grad_means, grad_inv_cov,
+                            grad_attr, grad_cam, self.workspace)
+        else:
+            voge_render_bwd_w(self.cams, params, means, inv_cov, attr, index, weights, grad_image, grad_means,
+                              grad_inv_cov, grad_attr, grad_cam, self.workspace)
 
 
 class VoGERender(torch.autograd.Function):
@@ -284,20 +304,20 @@ class VoGERender(torch.autograd.Function):
         image, weights, index = renderer.forward(means, inv_cov, attr)
         ctx.renderer = renderer
         ctx.cam_grad = cam_grad
-        ctx.save_for_backward(means, inv_cov, attr, index)
+        ctx.save_for_backward(means, inv_cov, attr, index, weights)
         ctx.mark_non_differentiable(weights, index)
         return image, weights, index
 
     @staticmethod
     def backward(ctx, grad_image, grad_w=None, grad_i=None):
-        means, inv_cov, attr, index = ctx.saved_tensors
+        means, inv_cov, attr, index, weights = ctx.saved_tensors
         r = ctx.renderer
         gm = torch.zeros_like(means) if ctx.needs_input_grad[0] else None
         gp = torch.zeros_like(inv_cov) if ctx.needs_input_grad[1] else None
         ga = torch.zeros_like(attr) if ctx.needs_input_grad[2] else None
         if grad_image is None:
             return gm, gp, ga, None, None
-        r.backward(means, inv_cov, attr, index, grad_image.contiguous(), gm, gp, ga, ctx.cam_grad)
+        r.backward(means, inv_cov, attr, index, grad_image.contiguous(), gm, gp, ga, ctx.cam_grad, weights=weights)
         return gm, gp, ga, None, None
 
 

@@ -35,12 +35,13 @@ def gpu_forward(cams, means, inv_cov, attr, K, tau, eta, flags=0, bin_capacity=0
     return r, (m, p, a), image.cpu().numpy(), weights.cpu().numpy()[:, : r.L], index.cpu().numpy()[:, : r.L]
 
 
-def gpu_backward(r, dev_inputs, index_np, grad_image_np, want_cam=True):
+def gpu_backward(r, dev_inputs, index_np, grad_image_np, want_cam=True, weights_np=None):
     m, p, a = dev_inputs
     gm, gp, ga = torch.zeros_like(m), torch.zeros_like(p), torch.zeros_like(a)
     gc = torch.zeros((r.params.B, 12), device="cuda") if want_cam else None
     idx = to_dev(index_np, torch.int32)
-    r.backward(m, p, a, idx, to_dev(grad_image_np), gm, gp, ga, gc)
+    w = None if weights_np is None else to_dev(np.ascontiguousarray(weights_np), torch.float32)
+    r.backward(m, p, a, idx, to_dev(grad_image_np), gm, gp, ga, gc, weights=w)
     torch.cuda.synchronize()
     out = {"g_means": gm.cpu().numpy(), "g_inv_cov": gp.cpu().numpy(), "g_attr": ga.cpu().numpy()}
     if want_cam:

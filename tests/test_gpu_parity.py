@@ -242,6 +242,43 @@ def test_backward_attribute_widths(C, K):
         assert rel_err(got[k], want[k]) <= TOL_GRAD, (k, rel_err(got[k], want[k]))
 
 
+@pytest.mark.parametrize("K", [16, 20, 32])
+def test_backward_with_forward_weights(K):
+    """voge_render_bwd_w (W_k from the forward) gives the gradients of the
+    recomputing backward and of the oracle."""
+    sc = scenes.fit_8x512(seed=50 + K, N=600, B=2, side=40)
+    cams, m, p, a = scene_inputs(sc)
+    p = p / 16.0
+    r, dev, img, w, idx = gpu_forward(cams, m, p, a, K, 1.0, 0.005)
+    g = np.random.default_rng(51).standard_normal(img.shape)
+    with_w = gpu_backward(r, dev, idx, g, weights_np=w)
+    without = gpu_backward(r, dev, idx, g)
+    want = oracle.render_bwd(cams, m, p, a, 1.0, oracle.all_pixels(cams), idx, g)
+    for k in ("g_means", "g_inv_cov", "g_attr", "g_R", "g_T"):
+        assert rel_err(with_w[k], without[k]) <= 1e-4, k
+        assert rel_err(with_w[k], want[k]) <= TOL_GRAD, k
+
+
+def test_backward_attribute_gradient_alone():
+    """Asking for the attribute gradient only (narrow attributes are folded in
+    by the finalize step) gives the same values as asking for everything."""
+    voge = lib_ready()
+    sc = scenes.fit_8x512(seed=60, N=500, B=3, side=40)
+    cams, m, p, a = scene_inputs(sc)
+    p = p / 16.0
+    r, dev, img, w, idx = gpu_forward(cams, m, p, a, 20, 1.0, 0.005)
+    g = to_dev(np.random.default_rng(61).standard_normal(img.shape))
+    mm, pp, aa = dev
+    i = to_dev(idx, torch.int32)
+    ga_only = torch.zeros_like(aa)
+    r.backward(mm, pp, aa, i, g, None, None, ga_only, None)
+    gm, gp, ga, gc = torch.zeros_like(mm), torch.zeros_like(pp), torch.zeros_like(aa), torch.zeros((3, 12), device="cuda")
+    r.backward(mm, pp, aa, i, g, gm, gp, ga, gc)
+    torch.cuda.synchronize()
+    assert float(ga.abs().max()) > 0
+    assert rel_err(ga_only.cpu().numpy(), ga.cpu().numpy()) <= 1e-5
+
+
 def test_backward_posefit_features():
     """C=128 features, K=20: attribute and camera gradients of the pose-fitting workload."""
     sc = scenes.posefit_256(seed=4, N=1500)
