@@ -245,9 +245,11 @@ __device__ __forceinline__ bool tile_sorted(int use_thresh, int plain, int cnt, 
 // One block sorts one tile list at a time.  Each entry is one 64-bit word,
 // (order-preserving bits of lmin) << 32 | index, so one compare orders by
 // (lmin, index) and a swap moves key and index together.  The list is padded
-// with all-ones words to a power of two; the bitonic network gives every
-// thread n/2/256 compare-exchanges per stage, with a block barrier between
-// stages.
+// with all-ones words to a power of two n and sorted by the bitonic network
+// with the entries in registers: thread t holds entries [tE, tE + E)
+// (E = n / 256, at least 1).  Exchanges at distance j < E stay inside a
+// thread, E <= j < 32E go through warp shuffles and only j >= 32E through
+// shared memory, with a block barrier on each side.
 constexpr int kSortThreads = 256;
 
 __device__ __forceinline__ uint64_t sort_word(float key, int32_t g) {
@@ -256,9 +258,76 @@ __device__ __forceinline__ uint64_t sort_word(float key, int32_t g) {
     return ((uint64_t)b << 32) | (uint32_t)g;
 }
 
+// Keeps the smaller (take_min) or the larger of (mine, other).
+__device__ __forceinline__ uint64_t keep(uint64_t mine, uint64_t other, bool take_min) {
+    return take_min ? (other < mine ? other : mine) : (other > mine ? other : mine);
+}
+
+template <int E>
+__device__ __forceinline__ void sort_tile_block(const Args& a, uint64_t* sw, int cnt, int off, int n2, int64_t vb) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nthr = n2 / E;  // threads holding entries (a multiple of 32 or all of n2 < 32)
+    const bool act = tid < nthr;
+    uint64_t w[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int x = tid * E + r;
+        w[r] = ~0ull;
+        if (act && x < cnt) {
+            const int32_t g = a.ws.tile_gauss[off + x];
+            w[r] = sort_word(__ldg(&a.ws.rec[4 * (vb + g) + 3].w), g);
+        }
+    }
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int b = 1; b < E; b <<= 1) {
+                    if (j == b) {
+#pragma unroll
+                        for (int r = 0; r < E; ++r) {
+                            if (r & b) continue;
+                            const bool up = ((tid * E + r) & k) == 0;
+                            const uint64_t lo = w[r], hi = w[r | b];
+                            const bool sw2 = (lo > hi) == up;
+                            w[r] = sw2 ? hi : lo;
+                            w[r | b] = sw2 ? lo : hi;
+                        }
+                    }
+                }
+            } else if (j < 32 * E && nthr >= 32) {
+                const int lm = j / E;  // partner lane distance
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, w[r], lm);
+                    const int x = tid * E + r;
+                    w[r] = keep(w[r], o, ((x & j) == 0) == ((x & k) == 0));
+                }
+            } else {
+                // partner in another warp (or lists shorter than a warp)
+                if (act)
+#pragma unroll
+                    for (int r = 0; r < E; ++r) sw[tid * E + r] = w[r];
+                __syncthreads();
+                if (act)
+#pragma unroll
+                    for (int r = 0; r < E; ++r) {
+                        const int x = tid * E + r;
+                        w[r] = keep(w[r], sw[x ^ j], ((x & j) == 0) == ((x & k) == 0));
+                    }
+                __syncthreads();
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int x = tid * E + r;
+        if (act && x < cnt) a.ws.tile_gauss[off + x] = (int32_t)(uint32_t)w[r];
+    }
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
-    __shared__ uint64_t w[kSortMax];
-    const int tid = threadIdx.x;
+    __shared__ uint64_t sw[kSortMax];
     const int nv = a.hdr->nviews, total = a.hdr->total_tiles;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int cnt = a.ws.tile_cnt[t];
@@ -268,30 +337,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
         int n2 = 2;
         while (n2 < cnt) n2 <<= 1;
         const int64_t vb = vd.rec_base;
-        for (int x = tid; x < n2; x += kSortThreads) {
-            uint64_t v = ~0ull;
-            if (x < cnt) {
-                const int32_t g = a.ws.tile_gauss[off + x];
-                v = sort_word(__ldg(&a.ws.rec[4 * (vb + g) + 3].w), g);
-            }
-            w[x] = v;
-        }
-        __syncthreads();
-        for (int k = 2; k <= n2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int q = tid; q < (n2 >> 1); q += kSortThreads) {
-                    const int x = 2 * q - (q & (j - 1));  // lower element of pair q at distance j
-                    const int y = x + j;
-                    const uint64_t wx = w[x], wy = w[y];
-                    const bool sw = (wx > wy) == ((x & k) == 0);
-                    w[x] = sw ? wy : wx;
-                    w[y] = sw ? wx : wy;
-                }
-                __syncthreads();
-            }
-        }
-        for (int x = tid; x < cnt; x += kSortThreads) a.ws.tile_gauss[off + x] = (int32_t)(uint32_t)w[x];
-        __syncthreads();  // the next tile reuses w
+        if (n2 <= 256) sort_tile_block<1>(a, sw, cnt, off, n2, vb);
+        else if (n2 == 512) sort_tile_block<2>(a, sw, cnt, off, n2, vb);
+        else if (n2 == 1024) sort_tile_block<4>(a, sw, cnt, off, n2, vb);
+        else sort_tile_block<8>(a, sw, cnt, off, n2, vb);
+        __syncthreads();  // the next tile reuses sw
     }
 }
 
