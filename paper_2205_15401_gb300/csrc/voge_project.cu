@@ -166,52 +166,77 @@ __global__ void __launch_bounds__(256) k_project(Args a, int count_tiles) {
     }
 }
 
-// Exclusive scan of the per-(tile, sub-counter) counts in tile order (one CTA
-// of 1024 threads; each thread owns a contiguous run of tiles).  Writes each
-// tile's count and first entry, and turns the sub-counts into the scatter
-// cursors (a tile's list is its sub-lists back to back).
+// Per tile: the total of its sub-counts (tile_cnt) and their exclusive
+// prefix within the tile (in place: the scatter cursors relative to the
+// tile's first entry).  One thread per tile.
+__global__ void __launch_bounds__(256) k_tile_totals(Args a) {
+    static_assert(kTileSub == 8, "two 16-byte vectors of sub-counts per tile");
+    const int n = a.hdr->total_tiles;
+    int4* sub4 = reinterpret_cast<int4*>(a.ws.tile_sub);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int4 u = sub4[2 * t], v = sub4[2 * t + 1];
+        int4 cu, cv;
+        cu.x = 0;
+        cu.y = u.x;
+        cu.z = cu.y + u.y;
+        cu.w = cu.z + u.z;
+        cv.x = cu.w + u.w;
+        cv.y = cv.x + v.x;
+        cv.z = cv.y + v.y;
+        cv.w = cv.z + v.z;
+        sub4[2 * t] = cu;
+        sub4[2 * t + 1] = cv;
+        a.ws.tile_cnt[t] = cv.w + v.w;
+    }
+}
+
+// Exclusive scan of tile_cnt into tile_off (one CTA of 1024 threads, rounds
+// of 4096 tiles, four consecutive tiles per thread).
 __global__ void __launch_bounds__(1024) k_scan_tiles(Args a) {
     __shared__ int32_t warp_sums[32];
-    const Ws& ws = a.ws;
     const int n = a.hdr->total_tiles;
-    const int tid = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int beg = min(n, tid * per), end = min(n, beg + per);
-    int32_t s = 0;
-    for (int q = beg; q < end; ++q)
-#pragma unroll
-        for (int u = 0; u < kTileSub; ++u) s += ws.tile_sub[q * kTileSub + u];
-    // block exclusive scan of s
-    int32_t x = s;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int32_t w = warp_sums[lane];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int32_t carry = 0;
+    for (int base = 0; base < n; base += 4 * 1024) {
+        const int q = base + 4 * tid;
+        int4 c = make_int4(0, 0, 0, 0);
+        if (q + 3 < n) {
+            c = *reinterpret_cast<const int4*>(a.ws.tile_cnt + q);
+        } else {
+            if (q < n) c.x = a.ws.tile_cnt[q];
+            if (q + 1 < n) c.y = a.ws.tile_cnt[q + 1];
+            if (q + 2 < n) c.z = a.ws.tile_cnt[q + 2];
+        }
+        const int32_t s = (c.x + c.y) + (c.z + c.w);
+        int32_t x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    int32_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0);
-    for (int q = beg; q < end; ++q) {
-        ws.tile_off[q] = run;
-        const int32_t first = run;
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t w = warp_sums[lane];
 #pragma unroll
-        for (int u = 0; u < kTileSub; ++u) {
-            const int32_t c = ws.tile_sub[q * kTileSub + u];
-            ws.tile_sub[q * kTileSub + u] = run;
-            run += c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
         }
-        ws.tile_cnt[q] = run - first;
+        __syncthreads();
+        const int32_t first = carry + x - s + (wid > 0 ? warp_sums[wid - 1] : 0);
+        const int4 o4 = make_int4(first, first + c.x, first + c.x + c.y, first + c.x + c.y + c.z);
+        if (q + 3 < n) {
+            *reinterpret_cast<int4*>(a.ws.tile_off + q) = o4;
+        } else {
+            if (q < n) a.ws.tile_off[q] = o4.x;
+            if (q + 1 < n) a.ws.tile_off[q + 1] = o4.y;
+            if (q + 2 < n) a.ws.tile_off[q + 2] = o4.z;
+        }
+        carry += warp_sums[31];
+        __syncthreads();  // warp_sums is rewritten by the next round
     }
 }
 
@@ -228,7 +253,8 @@ __global__ void __launch_bounds__(256) k_scatter(Args a) {
         const int sub = g & (kTileSub - 1);
         for (int ty = tb.z; ty <= tb.w; ++ty)
             for (int tx = tb.x; tx <= tb.y; ++tx) {
-                const int pos = atomicAdd(&a.ws.tile_sub[(tile_base + ty * tiles_x + tx) * kTileSub + sub], 1);
+                const int tile = tile_base + ty * tiles_x + tx;
+                const int pos = __ldg(a.ws.tile_off + tile) + atomicAdd(&a.ws.tile_sub[tile * kTileSub + sub], 1);
                 if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
             }
     }
@@ -358,6 +384,7 @@ cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s,
     if (count_tiles) {
         {
             TraceScope tr("k_scan_tiles", s);
+            k_tile_totals<<<tiles < 1 ? 1 : (tiles + 255) / 256, 256, 0, s>>>(a);
             k_scan_tiles<<<1, 1024, 0, s>>>(a);
         }
         {
