@@ -119,6 +119,17 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     // rows were just read, so these hit in cache).
     float hi[KM], lo[KM], dA[KM], dl[KM];
     int n = 0;
+    // With the forward's weights and narrow attributes, dA_k is formed while
+    // the entries are set up (the index is in a register there).
+    const float* wi = vd.weights_in ? vd.weights_in + pix * L : nullptr;
+    const bool early = wi != nullptr && C <= 3 && AM != kAttrWarp && AM != kAttrLane;
+    float ga0 = 0.0f, ga1 = 0.0f, ga2 = 0.0f;
+    if (early && valid) {
+        const float* gp0 = vd.grad_image + pix * C;
+        ga0 = __ldg(gp0);
+        if (C > 1) ga1 = __ldg(gp0 + 1);
+        if (C > 2) ga2 = __ldg(gp0 + 2);
+    }
     {
         int32_t id[KM];
 #pragma unroll
@@ -139,6 +150,16 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
                 hi[s] = e.hi;
                 lo[s] = e.lo;
                 jst[n * NT + tid] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
+                if (early) {
+                    const float* ck = attr + (int64_t)g * C;
+                    float G = ga0 * __ldg(ck);
+                    if (C > 1) G = fmaf(ga1, __ldg(ck + 1), G);
+                    if (C > 2) G = fmaf(ga2, __ldg(ck + 2), G);
+                    const float Wk = __ldg(wi + (s - (KM - K)));
+                    dA[s] = -tau * G * Wk;
+                    if (AM == kAttrChain) swk[n * NT + tid] = Wk;
+                    if (AM == kAttrSlot) red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * ga0, Wk * ga1, Wk * ga2);
+                }
                 ++n;
             } else if (s >= KM - K) {
                 open = false;
@@ -148,7 +169,6 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     const int32_t* li = vd.index_in + pix * L;
     auto kept = [&](int s) { return s >= KM - K && s - (KM - K) < n; };
     // loop 1: A_k (skipped when the forward's W_k are supplied)
-    const float* wi = vd.weights_in ? vd.weights_in + pix * L : nullptr;
     float A[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s) A[s] = 0.0f;
@@ -170,7 +190,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     const int sub = C <= 32 ? lane / C : 0;
     const int cc = C <= 32 ? lane - sub * C : lane;
     const int64_t pbase = (int64_t)(ty * TH + 2 * warp) * W + tx * kTileW;
-    {
+    if (!early) {
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
