@@ -55,10 +55,11 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const 
 // How a tile adds the attribute gradient dL/dc_g += W_k dL/dI:
 //   kAttrLane:  one reduction per lane and channel (4 <= C < 8),
 //   kAttrWarp:  warp-cooperative rows, lanes over (source pixel, channel) (C >= 8),
-//   kAttrChain: C <= 3, W_k kept in shared memory and added with the third
-//               camera-space vector reduction of the chain rule (slots 9..11
-//               of the record's 12 floats, free otherwise), folded into
-//               grad_attr by the finalize kernel,
+//   kAttrChain: C <= 3, W_k (the forward's weights when supplied, else kept
+//               in shared memory) added with the third camera-space vector
+//               reduction of the chain rule (slots 9..11 of the record's 12
+//               floats, free otherwise), folded into grad_attr by the
+//               finalize kernel,
 //   kAttrSlot:  C <= 3 for classes without room for W_k in shared memory: the
 //               same slots, with one vector reduction of their own.
 constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3;
@@ -157,7 +158,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
                     if (C > 2) G = fmaf(ga2, __ldg(ck + 2), G);
                     const float Wk = __ldg(wi + (s - (KM - K)));
                     dA[s] = -tau * G * Wk;
-                    if (AM == kAttrChain) swk[n * NT + tid] = Wk;
+                    if (AM == kAttrChain && !wi) swk[n * NT + tid] = Wk;
                     if (AM == kAttrSlot) red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * ga0, Wk * ga1, Wk * ga2);
                 }
                 ++n;
@@ -207,7 +208,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
                     if (AM == kAttrLane && grad_attr) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
                 }
                 dA[s] = -tau * G * Wk;
-                if (AM == kAttrChain) swk[e * NT + tid] = Wk;
+                if (AM == kAttrChain && !wi) swk[e * NT + tid] = Wk;
                 if (AM == kAttrSlot) {
                     const float g0 = __ldg(gp), g1 = C > 1 ? __ldg(gp + 1) : 0.0f, g2 = C > 2 ? __ldg(gp + 2) : 0.0f;
                     red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * g0, Wk * g1, Wk * g2);
@@ -292,7 +293,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
         red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
         if (AM == kAttrChain) {
-            const float wk = swk[e * NT + tid];
+            const float wk = wi ? __ldg(wi + e) : swk[e * NT + tid];
             red_add_v4(gc + 8, gv[8], wk * gi0, wk * gi1, wk * gi2);
         } else {
             red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
@@ -306,10 +307,11 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
     for (;;) {
         const int t = next_tile(a, 0, &s_slot);
         if (t < 0) return;
-        const int C = a.views[view_of_tile(a.views, a.hdr->nviews, t)].C;
+        const ViewDesc& vd = a.views[view_of_tile(a.views, a.hdr->nviews, t)];
+        const int C = vd.C;
         if (C >= 8) backward_tile<KM, TH, kAttrWarp>(a, t);
         else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t);
-        else if constexpr (wk_in_smem<KM, TH>()) backward_tile<KM, TH, kAttrChain>(a, t);
+        else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t);
         else backward_tile<KM, TH, kAttrSlot>(a, t);
     }
 }
@@ -524,8 +526,8 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
 }
 
 template <int KM, int TH>
-static size_t backward_smem_bytes() {
-    return (size_t)KM * 16 * TH * (wk_in_smem<KM, TH>() ? 20 : 16);
+static size_t backward_smem_bytes(bool with_wk = true) {
+    return (size_t)KM * 16 * TH * (with_wk && wk_in_smem<KM, TH>() ? 20 : 16);
 }
 
 template <typename Kern>
@@ -549,13 +551,18 @@ int backward_blocks_per_sm(int KM) {
 }
 
 // Launch the backward tile kernel for register-list capacity KM (0 = generic).
-cudaError_t launch_backward_tiles(int KM, int nblocks, cudaStream_t s, const Args& a) {
+cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, cudaStream_t s, const Args& a0) {
+    // with_wk = 0: every view brings the forward's weights, so the W_k buffer
+    // is left out and its shared memory goes to L1 (the chain's record reads)
+    Args a = a0;
+    a.wk_smem = with_wk ? 1 : 0;
+    const bool w = with_wk != 0;
     switch (KM) {
-        case 8: return launch_tiles(k_backward<8, 16>, "k_backward<8>", nblocks, 256, backward_smem_bytes<8, 16>(), s, a);
-        case 16: return launch_tiles(k_backward<16, 16>, "k_backward<16>", nblocks, 256, backward_smem_bytes<16, 16>(), s, a);
-        case 20: return launch_tiles(k_backward<20, 16>, "k_backward<20>", nblocks, 256, backward_smem_bytes<20, 16>(), s, a);
-        case 24: return launch_tiles(k_backward<24, 16>, "k_backward<24>", nblocks, 256, backward_smem_bytes<24, 16>(), s, a);
-        case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, backward_smem_bytes<32, 8>(), s, a);
+        case 8: return launch_tiles(k_backward<8, 16>, "k_backward<8>", nblocks, 256, backward_smem_bytes<8, 16>(w), s, a);
+        case 16: return launch_tiles(k_backward<16, 16>, "k_backward<16>", nblocks, 256, backward_smem_bytes<16, 16>(w), s, a);
+        case 20: return launch_tiles(k_backward<20, 16>, "k_backward<20>", nblocks, 256, backward_smem_bytes<20, 16>(w), s, a);
+        case 24: return launch_tiles(k_backward<24, 16>, "k_backward<24>", nblocks, 256, backward_smem_bytes<24, 16>(w), s, a);
+        case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, backward_smem_bytes<32, 8>(w), s, a);
         default: return launch_tiles(k_backward_generic, "k_backward_generic", nblocks, 256, 0, s, a);
     }
 }

@@ -378,6 +378,7 @@ struct Args {
     BatchHdr* hdr;
     Ws ws;
     int32_t cls;      // list-capacity class of a tile launch (index into class_begin/end)
+    int32_t wk_smem;  // backward launches: the W_k buffer follows the stream in shared memory
 };
 
 // Next tile of a persistent tile launch (dynamic: CTAs take tiles as they
