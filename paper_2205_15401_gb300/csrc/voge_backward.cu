@@ -66,10 +66,13 @@ constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3;
 
 // Classes whose W_k buffer fits next to the stream without losing a block per SM.
 template <int KM, int TH>
-__host__ __device__ constexpr bool wk_in_smem() { return TH == 16 && KM <= 20; }
+__host__ __device__ constexpr bool wk_in_smem() { return KM <= 20; }
 
+// One backward tile: rows [hb TH, hb TH + TH) of binning tile t (the
+// backward reads the index lists, not the tile lists, so it may split the
+// forward's tiles into shorter ones).
 template <int KM, int TH, int AM>
-__device__ __forceinline__ void backward_tile(const Args& a, int t) {
+__device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     float4* jst = smem;  // [KM][NT]
@@ -83,8 +86,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     const int H = vd.H, W = vd.W;
     const float invF = vd.invF;
     const int tid = threadIdx.x;
+    const int row0 = ty * vd.tile_h + hb * TH;  // first pixel row of this backward tile
     const int j = tx * kTileW + (tid & 15);
-    const int i = ty * TH + (tid >> 4);
+    const int i = row0 + (tid >> 4);
     const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
     const int64_t pix = (int64_t)i * W + j;
@@ -105,7 +109,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
         const int ncols = min(kTileW, W - tx * kTileW);
 #pragma unroll
         for (int rw = 0; rw < 2; ++rw) {
-            const int irow = ty * TH + 2 * warp + rw;
+            const int irow = row0 + 2 * warp + rw;
             const int cnt = irow < H ? ncols * L : 0;
             const int32_t* src = vd.index_in + ((int64_t)irow * W + tx * kTileW) * L;
             for (int x = lane; x < 16 * L; x += 32) *stg(rw * 16 * L + x) = x < cnt ? __ldg(src + x) : -1;
@@ -190,7 +194,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     const int spi = C <= 32 ? 32 / C : 1;  // source lanes per step
     const int sub = C <= 32 ? lane / C : 0;
     const int cc = C <= 32 ? lane - sub * C : lane;
-    const int64_t pbase = (int64_t)(ty * TH + 2 * warp) * W + tx * kTileW;
+    const int64_t pbase = (int64_t)(row0 + 2 * warp) * W + tx * kTileW;
     if (!early) {
         int e = 0;
 #pragma unroll
@@ -301,18 +305,29 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t) {
     }
 }
 
+// Backward tiles are 16 x TH (TH = 8): each binning tile of tile_h rows is
+// split into tile_h / TH of them, so a CTA of 128 threads keeps more
+// registers per thread and less shared memory (more L1) than one per
+// binning tile.
 template <int KM, int TH>
 __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) {
     __shared__ int s_slot;
+    // every view of one class launch has the same tile height (a serving tick
+    // mixes classes, so take it from this class's first tile)
+    const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
     for (;;) {
-        const int t = next_tile(a, 0, &s_slot);
-        if (t < 0) return;
+        if (threadIdx.x == 0) s_slot = atomicAdd(&a.hdr->counters[a.cls + kMaxClasses], 1);
+        __syncthreads();
+        const int tb = R * a.hdr->class_begin[a.cls] + s_slot;
+        __syncthreads();
+        if (tb >= R * a.hdr->class_end[a.cls]) return;
+        const int t = tb / R, hb = tb - t * R;
         const ViewDesc& vd = a.views[view_of_tile(a.views, a.hdr->nviews, t)];
         const int C = vd.C;
-        if (C >= 8) backward_tile<KM, TH, kAttrWarp>(a, t);
-        else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t);
-        else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t);
-        else backward_tile<KM, TH, kAttrSlot>(a, t);
+        if (C >= 8) backward_tile<KM, TH, kAttrWarp>(a, t, hb);
+        else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t, hb);
+        else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t, hb);
+        else backward_tile<KM, TH, kAttrSlot>(a, t, hb);
     }
 }
 
@@ -517,7 +532,7 @@ template <typename Kern>
 static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthreads, size_t smem, cudaStream_t s,
                                 const Args& a) {
     TraceScope tr(name, s);
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {  // opt in well below 48 KB: the kernels' static shared memory counts too
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -532,7 +547,7 @@ static size_t backward_smem_bytes(bool with_wk = true) {
 
 template <typename Kern>
 static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nthreads, smem) != cudaSuccess || nb < 1) nb = 1;
     return nb;
@@ -541,10 +556,10 @@ static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
 // Resident CTAs per SM of the backward tile kernel for capacity KM.
 int backward_blocks_per_sm(int KM) {
     switch (KM) {
-        case 8: return blocks_per_sm(k_backward<8, 16>, 256, backward_smem_bytes<8, 16>());
-        case 16: return blocks_per_sm(k_backward<16, 16>, 256, backward_smem_bytes<16, 16>());
-        case 20: return blocks_per_sm(k_backward<20, 16>, 256, backward_smem_bytes<20, 16>());
-        case 24: return blocks_per_sm(k_backward<24, 16>, 256, backward_smem_bytes<24, 16>());
+        case 8: return blocks_per_sm(k_backward<8, 8>, 128, backward_smem_bytes<8, 8>());
+        case 16: return blocks_per_sm(k_backward<16, 8>, 128, backward_smem_bytes<16, 8>());
+        case 20: return blocks_per_sm(k_backward<20, 8>, 128, backward_smem_bytes<20, 8>());
+        case 24: return blocks_per_sm(k_backward<24, 8>, 128, backward_smem_bytes<24, 8>());
         case 32: return blocks_per_sm(k_backward<32, 8>, 128, backward_smem_bytes<32, 8>());
         default: return blocks_per_sm(k_backward_generic, 256, 0);
     }
@@ -558,10 +573,10 @@ cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, cudaStream_t
     a.wk_smem = with_wk ? 1 : 0;
     const bool w = with_wk != 0;
     switch (KM) {
-        case 8: return launch_tiles(k_backward<8, 16>, "k_backward<8>", nblocks, 256, backward_smem_bytes<8, 16>(w), s, a);
-        case 16: return launch_tiles(k_backward<16, 16>, "k_backward<16>", nblocks, 256, backward_smem_bytes<16, 16>(w), s, a);
-        case 20: return launch_tiles(k_backward<20, 16>, "k_backward<20>", nblocks, 256, backward_smem_bytes<20, 16>(w), s, a);
-        case 24: return launch_tiles(k_backward<24, 16>, "k_backward<24>", nblocks, 256, backward_smem_bytes<24, 16>(w), s, a);
+        case 8: return launch_tiles(k_backward<8, 8>, "k_backward<8>", nblocks, 128, backward_smem_bytes<8, 8>(w), s, a);
+        case 16: return launch_tiles(k_backward<16, 8>, "k_backward<16>", nblocks, 128, backward_smem_bytes<16, 8>(w), s, a);
+        case 20: return launch_tiles(k_backward<20, 8>, "k_backward<20>", nblocks, 128, backward_smem_bytes<20, 8>(w), s, a);
+        case 24: return launch_tiles(k_backward<24, 8>, "k_backward<24>", nblocks, 128, backward_smem_bytes<24, 8>(w), s, a);
         case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, backward_smem_bytes<32, 8>(w), s, a);
         default: return launch_tiles(k_backward_generic, "k_backward_generic", nblocks, 256, 0, s, a);
     }

@@ -31,6 +31,18 @@ namespace voge {
 constexpr int kTileW = 16;     // tile width in pixels (one warp covers 16 x 2 pixels)
 constexpr int kSortMax = 2048; // tiles with more candidates are processed unsorted
 constexpr int kTileSub = 8;    // counters per tile for binning (spreads same-address atomics)
+constexpr int kSortPosBits = 11;  // list positions of a sorted tile (kSortMax = 2^11)
+static_assert(kSortMax == 1 << kSortPosBits, "sort words hold a list position in their low bits");
+
+// Order-preserving map between floats and unsigned integers: a < b exactly
+// when float_order(a) < float_order(b) (for non-NaN a, b).
+__device__ __forceinline__ uint32_t float_order(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_float(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
 constexpr float kLog2e = 1.4426950408889634f;
 
 // One view as the kernels read it: the camera, the scene this view renders

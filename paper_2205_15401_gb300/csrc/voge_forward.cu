@@ -543,7 +543,7 @@ template <typename Kern>
 static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthreads, size_t smem, cudaStream_t s,
                                 const Args& a) {
     TraceScope tr(name, s);
-    if (smem > 48 * 1024) {
+    if (smem > 32 * 1024) {  // opt in well below 48 KB: the kernels' static shared memory counts too
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -553,7 +553,7 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
 
 template <typename Kern>
 static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nthreads, smem) != cudaSuccess || nb < 1) nb = 1;
     return nb;

@@ -98,6 +98,10 @@ __device__ __forceinline__ void project_one(const Args& a, int v, int64_t t, int
         if (use_thresh && detP > 0.0f && a22 > 0.0f) {
             const float h = sqrtf(Qeta * a22 / detP);
             lmin = Mz.hi - (1.001f * h + 1e-6f * Mz.hi);
+            // snapped down to a multiple of 2^11 in the order-preserving
+            // integer map: still a lower bound, and the tile sort keys the
+            // list position into the freed low bits
+            lmin = order_float(float_order(lmin) & ~((1u << kSortPosBits) - 1u));
         }
         r3 = make_float4(s2 * c22, Mz.hi, Mz.lo, lmin);
         s1.z = x;
@@ -268,40 +272,38 @@ __device__ __forceinline__ bool tile_sorted(int use_thresh, int plain, int cnt, 
     return use_thresh && !plain && cnt > 1 && cnt <= kSortMax && off + cnt <= cap;
 }
 
-// One block sorts one tile list at a time.  Each entry is one 64-bit word,
-// (order-preserving bits of lmin) << 32 | index, so one compare orders by
-// (lmin, index) and a swap moves key and index together.  The list is padded
-// with all-ones words to a power of two n and sorted by the bitonic network
-// with the entries in registers: thread t holds entries [tE, tE + E)
-// (E = n / 256, at least 1).  Exchanges at distance j < E stay inside a
-// thread, E <= j < 32E go through warp shuffles and only j >= 32E through
-// shared memory, with a block barrier on each side.
+// One block sorts one tile list at a time.  Each entry is one 32-bit word,
+// (order-preserving bits of lmin, whose low kSortPosBits bits k_project
+// cleared) | (the entry's position in the unsorted list), so one compare
+// orders by (lmin, position) and the sorted words give back the Gaussians
+// through a table of the unsorted list.  The list is padded with all-ones
+// words to a power of two n and sorted by the bitonic network with the words
+// in registers: thread t holds words [tE, tE + E) (E = n / 256, at least 1).
+// Exchanges at distance j < E stay inside a thread, E <= j < 32E go through
+// warp shuffles and only j >= 32E through shared memory, with a block barrier
+// on each side.
 constexpr int kSortThreads = 256;
 
-__device__ __forceinline__ uint64_t sort_word(float key, int32_t g) {
-    uint32_t b = __float_as_uint(key);
-    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-    return ((uint64_t)b << 32) | (uint32_t)g;
-}
-
 // Keeps the smaller (take_min) or the larger of (mine, other).
-__device__ __forceinline__ uint64_t keep(uint64_t mine, uint64_t other, bool take_min) {
-    return take_min ? (other < mine ? other : mine) : (other > mine ? other : mine);
+__device__ __forceinline__ uint32_t keep(uint32_t mine, uint32_t other, bool take_min) {
+    return take_min ? min(mine, other) : max(mine, other);
 }
 
 template <int E>
-__device__ __forceinline__ void sort_tile_block(const Args& a, uint64_t* sw, int cnt, int off, int n2, int64_t vb) {
-    const int tid = threadIdx.x, lane = tid & 31;
+__device__ __forceinline__ void sort_tile_block(const Args& a, uint32_t* sw, int32_t* sg, int cnt, int off, int n2,
+                                                int64_t vb) {
+    const int tid = threadIdx.x;
     const int nthr = n2 / E;  // threads holding entries (a multiple of 32 or all of n2 < 32)
     const bool act = tid < nthr;
-    uint64_t w[E];
+    uint32_t w[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int x = tid * E + r;
-        w[r] = ~0ull;
+        w[r] = ~0u;
         if (act && x < cnt) {
             const int32_t g = a.ws.tile_gauss[off + x];
-            w[r] = sort_word(__ldg(&a.ws.rec[4 * (vb + g) + 3].w), g);
+            sg[x] = g;
+            w[r] = (float_order(__ldg(&a.ws.rec[4 * (vb + g) + 3].w)) & ~((1u << kSortPosBits) - 1u)) | (uint32_t)x;
         }
     }
     for (int k = 2; k <= n2; k <<= 1) {
@@ -314,10 +316,9 @@ __device__ __forceinline__ void sort_tile_block(const Args& a, uint64_t* sw, int
                         for (int r = 0; r < E; ++r) {
                             if (r & b) continue;
                             const bool up = ((tid * E + r) & k) == 0;
-                            const uint64_t lo = w[r], hi = w[r | b];
-                            const bool sw2 = (lo > hi) == up;
-                            w[r] = sw2 ? hi : lo;
-                            w[r | b] = sw2 ? lo : hi;
+                            const uint32_t lo = w[r], hi = w[r | b];
+                            w[r] = up ? min(lo, hi) : max(lo, hi);
+                            w[r | b] = up ? max(lo, hi) : min(lo, hi);
                         }
                     }
                 }
@@ -325,7 +326,7 @@ __device__ __forceinline__ void sort_tile_block(const Args& a, uint64_t* sw, int
                 const int lm = j / E;  // partner lane distance
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
-                    const uint64_t o = __shfl_xor_sync(0xffffffffu, w[r], lm);
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, w[r], lm);
                     const int x = tid * E + r;
                     w[r] = keep(w[r], o, ((x & j) == 0) == ((x & k) == 0));
                 }
@@ -345,15 +346,17 @@ __device__ __forceinline__ void sort_tile_block(const Args& a, uint64_t* sw, int
             }
         }
     }
+    __syncthreads();  // sg complete (written above by every thread)
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int x = tid * E + r;
-        if (act && x < cnt) a.ws.tile_gauss[off + x] = (int32_t)(uint32_t)w[r];
+        if (act && x < cnt) a.ws.tile_gauss[off + x] = sg[w[r] & ((1u << kSortPosBits) - 1u)];
     }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
-    __shared__ uint64_t sw[kSortMax];
+    __shared__ uint32_t sw[kSortMax];
+    __shared__ int32_t sg[kSortMax];
     const int nv = a.hdr->nviews, total = a.hdr->total_tiles;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int cnt = a.ws.tile_cnt[t];
@@ -363,11 +366,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
         int n2 = 2;
         while (n2 < cnt) n2 <<= 1;
         const int64_t vb = vd.rec_base;
-        if (n2 <= 256) sort_tile_block<1>(a, sw, cnt, off, n2, vb);
-        else if (n2 == 512) sort_tile_block<2>(a, sw, cnt, off, n2, vb);
-        else if (n2 == 1024) sort_tile_block<4>(a, sw, cnt, off, n2, vb);
-        else sort_tile_block<8>(a, sw, cnt, off, n2, vb);
-        __syncthreads();  // the next tile reuses sw
+        if (n2 <= 256) sort_tile_block<1>(a, sw, sg, cnt, off, n2, vb);
+        else if (n2 == 512) sort_tile_block<2>(a, sw, sg, cnt, off, n2, vb);
+        else if (n2 == 1024) sort_tile_block<4>(a, sw, sg, cnt, off, n2, vb);
+        else sort_tile_block<8>(a, sw, sg, cnt, off, n2, vb);
+        __syncthreads();  // the next tile reuses sw and sg
     }
 }
 
