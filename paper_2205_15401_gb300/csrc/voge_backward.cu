@@ -191,9 +191,13 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     const float ntl = -tau * kLog2e;
     const float* gp = vd.grad_image + pix * C;
     constexpr bool coop = AM == kAttrWarp;
-    const int spi = C <= 32 ? 32 / C : 1;  // source lanes per step
-    const int sub = C <= 32 ? lane / C : 0;
-    const int cc = C <= 32 ? lane - sub * C : lane;
+    // rows of 16-byte vectors when the widths and addresses allow
+    const bool rv4 = (C & 3) == 0 && ((reinterpret_cast<uintptr_t>(grad_attr) |
+                                       reinterpret_cast<uintptr_t>(vd.grad_image)) & 15) == 0;
+    const int cw = rv4 ? C >> 2 : C;         // row width in scatter units
+    const int spi = cw <= 32 ? 32 / cw : 1;  // source lanes per step
+    const int sub = cw <= 32 ? lane / cw : 0;
+    const int cc = cw <= 32 ? lane - sub * cw : lane;
     const int64_t pbase = (int64_t)(row0 + 2 * warp) * W + tx * kTileW;
     if (!early) {
         int e = 0;
@@ -206,10 +210,19 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                 Wk = wi ? __ldg(wi + (s - (KM - K))) : ex2_approx(ntl * A[s]) * (2.0f * jst[e * NT + tid].w);
                 const float* ck = attr + (int64_t)g * C;
                 float G = 0.0f;
-                for (int c = 0; c < C; ++c) {
-                    const float gc = __ldg(gp + c);
-                    G = fmaf(gc, __ldg(ck + c), G);
-                    if (AM == kAttrLane && grad_attr) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
+                if (AM == kAttrWarp && ((C & 3) | ((reinterpret_cast<uintptr_t>(attr) |
+                                                     reinterpret_cast<uintptr_t>(vd.grad_image)) & 15)) == 0) {
+                    for (int c = 0; c < (C >> 2); ++c) {
+                        const float4 x = __ldg(reinterpret_cast<const float4*>(gp) + c);
+                        const float4 y = __ldg(reinterpret_cast<const float4*>(ck) + c);
+                        G = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, G))));
+                    }
+                } else {
+                    for (int c = 0; c < C; ++c) {
+                        const float gc = __ldg(gp + c);
+                        G = fmaf(gc, __ldg(ck + c), G);
+                        if (AM == kAttrLane && grad_attr) atomicAdd(grad_attr + (int64_t)g * C + c, Wk * gc);
+                    }
                 }
                 dA[s] = -tau * G * Wk;
                 if (AM == kAttrChain && !wi) swk[e * NT + tid] = Wk;
@@ -230,7 +243,14 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                     if (sub < spi && src < 32 && gs >= 0) {
                         const float* gsrc = vd.grad_image + (pbase + (src >> 4) * W + (src & 15)) * C;
                         float* dst = grad_attr + (int64_t)gs * C;
-                        for (int c = cc; c < C; c += 32) atomicAdd(dst + c, ws * __ldg(gsrc + c));
+                        if (rv4) {
+                            for (int c = cc; c < cw; c += 32) {
+                                const float4 x = __ldg(reinterpret_cast<const float4*>(gsrc) + c);
+                                red_add_v4(dst + 4 * c, ws * x.x, ws * x.y, ws * x.z, ws * x.w);
+                            }
+                        } else {
+                            for (int c = cc; c < C; c += 32) atomicAdd(dst + c, ws * __ldg(gsrc + c));
+                        }
                     }
                 }
             }
@@ -308,15 +328,17 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
 // Backward tiles are 16 x TH (TH = 8): each binning tile of tile_h rows is
 // split into tile_h / TH of them, so a CTA of 128 threads keeps more
 // registers per thread and less shared memory (more L1) than one per
-// binning tile.
-template <int KM, int TH>
+// binning tile.  WIDE kernels take the views with C >= 8 (warp-cooperative
+// attribute rows), the others the rest; they are separate kernels so that
+// each gets its own register allocation.  Each skips the other's tiles.
+template <int KM, int TH, bool WIDE>
 __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) {
     __shared__ int s_slot;
     // every view of one class launch has the same tile height (a serving tick
     // mixes classes, so take it from this class's first tile)
     const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
     for (;;) {
-        if (threadIdx.x == 0) s_slot = atomicAdd(&a.hdr->counters[a.cls + kMaxClasses], 1);
+        if (threadIdx.x == 0) s_slot = atomicAdd(&a.hdr->counters[a.cls + (WIDE ? 2 : 1) * kMaxClasses], 1);
         __syncthreads();
         const int tb = R * a.hdr->class_begin[a.cls] + s_slot;
         __syncthreads();
@@ -324,7 +346,8 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) 
         const int t = tb / R, hb = tb - t * R;
         const ViewDesc& vd = a.views[view_of_tile(a.views, a.hdr->nviews, t)];
         const int C = vd.C;
-        if (C >= 8) backward_tile<KM, TH, kAttrWarp>(a, t, hb);
+        if ((C >= 8) != WIDE) continue;
+        if (WIDE) backward_tile<KM, TH, kAttrWarp>(a, t, hb);
         else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t, hb);
         else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t, hb);
         else backward_tile<KM, TH, kAttrSlot>(a, t, hb);
@@ -556,28 +579,39 @@ static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
 // Resident CTAs per SM of the backward tile kernel for capacity KM.
 int backward_blocks_per_sm(int KM) {
     switch (KM) {
-        case 8: return blocks_per_sm(k_backward<8, 8>, 128, backward_smem_bytes<8, 8>());
-        case 16: return blocks_per_sm(k_backward<16, 8>, 128, backward_smem_bytes<16, 8>());
-        case 20: return blocks_per_sm(k_backward<20, 8>, 128, backward_smem_bytes<20, 8>());
-        case 24: return blocks_per_sm(k_backward<24, 8>, 128, backward_smem_bytes<24, 8>());
-        case 32: return blocks_per_sm(k_backward<32, 8>, 128, backward_smem_bytes<32, 8>());
+        case 8: return blocks_per_sm(k_backward<8, 8, false>, 128, backward_smem_bytes<8, 8>());
+        case 16: return blocks_per_sm(k_backward<16, 8, false>, 128, backward_smem_bytes<16, 8>());
+        case 20: return blocks_per_sm(k_backward<20, 8, false>, 128, backward_smem_bytes<20, 8>());
+        case 24: return blocks_per_sm(k_backward<24, 8, false>, 128, backward_smem_bytes<24, 8>());
+        case 32: return blocks_per_sm(k_backward<32, 8, false>, 128, backward_smem_bytes<32, 8>());
         default: return blocks_per_sm(k_backward_generic, 256, 0);
     }
 }
 
 // Launch the backward tile kernel for register-list capacity KM (0 = generic).
-cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, cudaStream_t s, const Args& a0) {
+template <int KM>
+static cudaError_t launch_backward_pair(const char* name, const char* wname, int nblocks, bool w, int kinds,
+                                        cudaStream_t s, const Args& a) {
+    cudaError_t e = cudaSuccess;
+    if (kinds & 1) e = launch_tiles(k_backward<KM, 8, false>, name, nblocks, 128, backward_smem_bytes<KM, 8>(w), s, a);
+    if (e == cudaSuccess && (kinds & 2))
+        e = launch_tiles(k_backward<KM, 8, true>, wname, nblocks, 128, backward_smem_bytes<KM, 8>(w), s, a);
+    return e;
+}
+
+cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a0) {
     // with_wk = 0: every view brings the forward's weights, so the W_k buffer
-    // is left out and its shared memory goes to L1 (the chain's record reads)
+    // is left out and its shared memory goes to L1 (the chain's record reads).
+    // kinds: bit 0 launches the kernel for C < 8, bit 1 the one for C >= 8.
     Args a = a0;
     a.wk_smem = with_wk ? 1 : 0;
     const bool w = with_wk != 0;
     switch (KM) {
-        case 8: return launch_tiles(k_backward<8, 8>, "k_backward<8>", nblocks, 128, backward_smem_bytes<8, 8>(w), s, a);
-        case 16: return launch_tiles(k_backward<16, 8>, "k_backward<16>", nblocks, 128, backward_smem_bytes<16, 8>(w), s, a);
-        case 20: return launch_tiles(k_backward<20, 8>, "k_backward<20>", nblocks, 128, backward_smem_bytes<20, 8>(w), s, a);
-        case 24: return launch_tiles(k_backward<24, 8>, "k_backward<24>", nblocks, 128, backward_smem_bytes<24, 8>(w), s, a);
-        case 32: return launch_tiles(k_backward<32, 8>, "k_backward<32>", nblocks, 128, backward_smem_bytes<32, 8>(w), s, a);
+        case 8: return launch_backward_pair<8>("k_backward<8>", "k_backward<8,wide>", nblocks, w, kinds, s, a);
+        case 16: return launch_backward_pair<16>("k_backward<16>", "k_backward<16,wide>", nblocks, w, kinds, s, a);
+        case 20: return launch_backward_pair<20>("k_backward<20>", "k_backward<20,wide>", nblocks, w, kinds, s, a);
+        case 24: return launch_backward_pair<24>("k_backward<24>", "k_backward<24,wide>", nblocks, w, kinds, s, a);
+        case 32: return launch_backward_pair<32>("k_backward<32>", "k_backward<32,wide>", nblocks, w, kinds, s, a);
         default: return launch_tiles(k_backward_generic, "k_backward_generic", nblocks, 256, 0, s, a);
     }
 }

@@ -32,7 +32,7 @@
 namespace voge {
 cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
-cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, cudaStream_t s, const Args& a);
+cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int tile_grid(int KM, int fwd, int total_tiles);
 
@@ -358,7 +358,8 @@ cudaError_t issue_tick(voge_server* S, TickSlot& ts, uint32_t mask) {
         if (!(mask & (1u << c))) continue;
         Args ac = a;
         ac.cls = c;
-        e = launch_backward_tiles(kClassKM[c], tile_grid(kClassKM[c], 0, 1 << 30), 0, s, ac);  // ticks pass their weights
+        // ticks pass their weights; requests of both attribute kinds may share a class
+        e = launch_backward_tiles(kClassKM[c], tile_grid(kClassKM[c], 0, 1 << 30), 0, 3, s, ac);
         if (e != cudaSuccess) return e;
     }
     return launch_grad_finalize(S->grid_records, 0, 0, 0, s, a);
