@@ -276,7 +276,21 @@ __global__ void __launch_bounds__(256) k_mse(const float* x, const float* y, int
     __shared__ float red[8];
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool v4 = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(gx)) & 15) == 0;
+    int64_t done = 0;
+    if (v4) {  // 16-byte rows of four elements, then the tail
+        const int64_t n4 = n >> 2;
+        for (int64_t q = first; q < n4; q += stride) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(x) + q), b = __ldg(reinterpret_cast<const float4*>(y) + q);
+            const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+            acc = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, acc))));
+            reinterpret_cast<float4*>(gx)[q] = make_float4(2.0f * d.x * inv, 2.0f * d.y * inv, 2.0f * d.z * inv, 2.0f * d.w * inv);
+        }
+        done = n4 << 2;
+    }
+    for (int64_t q = done + first; q < n; q += stride) {
         const float d = x[q] - y[q];
         acc = fmaf(d, d, acc);
         gx[q] = 2.0f * d * inv;
@@ -293,17 +307,39 @@ __global__ void __launch_bounds__(256) k_mse(const float* x, const float* y, int
 
 // One Adam step (Kingma & Ba 2015) over n parameters, bias-corrected with
 // the 1-based step count; the gradient is zeroed once read.
+__device__ __forceinline__ void adam_one(float& x, float& g, float& m, float& v, float lr, float b1, float b2,
+                                         float eps, float c1, float c2) {
+    const float gq = g;
+    g = 0.0f;  // consumed: ready for the next accumulation
+    m = fmaf(b1, m - gq, gq);
+    v = fmaf(b2, v - gq * gq, gq * gq);
+    x -= lr * (m * c1) / (sqrtf(v * c2) + eps);
+}
+
 __global__ void __launch_bounds__(256) k_adam(float* x, float* g, float* m, float* v, int64_t n, float lr,
                                               float b1, float b2, float eps, float c1, float c2) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const float gq = g[q];
-        g[q] = 0.0f;  // consumed: ready for the next accumulation
-        const float mq = fmaf(b1, m[q] - gq, gq);
-        const float vq = fmaf(b2, v[q] - gq * gq, gq * gq);
-        m[q] = mq;
-        v[q] = vq;
-        x[q] -= lr * (mq * c1) / (sqrtf(vq * c2) + eps);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool v4 = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(m) |
+                      reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+    int64_t done = 0;
+    if (v4) {  // four parameters per thread and step, then the tail
+        const int64_t n4 = n >> 2;
+        for (int64_t q = first; q < n4; q += stride) {
+            float4 xq = reinterpret_cast<float4*>(x)[q], gq = reinterpret_cast<float4*>(g)[q];
+            float4 mq = reinterpret_cast<float4*>(m)[q], vq = reinterpret_cast<float4*>(v)[q];
+            adam_one(xq.x, gq.x, mq.x, vq.x, lr, b1, b2, eps, c1, c2);
+            adam_one(xq.y, gq.y, mq.y, vq.y, lr, b1, b2, eps, c1, c2);
+            adam_one(xq.z, gq.z, mq.z, vq.z, lr, b1, b2, eps, c1, c2);
+            adam_one(xq.w, gq.w, mq.w, vq.w, lr, b1, b2, eps, c1, c2);
+            reinterpret_cast<float4*>(x)[q] = xq;
+            reinterpret_cast<float4*>(g)[q] = gq;
+            reinterpret_cast<float4*>(m)[q] = mq;
+            reinterpret_cast<float4*>(v)[q] = vq;
+        }
+        done = n4 << 2;
     }
+    for (int64_t q = done + first; q < n; q += stride) adam_one(x[q], g[q], m[q], v[q], lr, b1, b2, eps, c1, c2);
 }
 
 }  // namespace

@@ -338,6 +338,46 @@ def test_mse_grad_kernel():
     np.testing.assert_allclose(g.cpu().numpy(), 2 * (x - y) / x.size, rtol=1e-5, atol=1e-9)
 
 
+@pytest.mark.parametrize("n,off", [(10007, 0), (4096, 1)])
+def test_mse_grad_kernel_sizes_and_alignment(n, off):
+    """The four-wide path, its tail, and unaligned views (scalar path)."""
+    voge = lib_ready()
+    rng = np.random.default_rng(19)
+    x, y = r32(rng.standard_normal(n + off)), r32(rng.standard_normal(n + off))
+    xd, yd = to_dev(x)[off:], to_dev(y)[off:]
+    g = torch.zeros(n + off, device="cuda")[off:]
+    loss = torch.zeros(1, device="cuda")
+    voge.voge_mse_grad(xd, yd, g, loss)
+    torch.cuda.synchronize()
+    d = (x[off:] - y[off:]).astype(np.float64)
+    assert float(loss) == pytest.approx(np.mean(d ** 2), rel=1e-5)
+    np.testing.assert_allclose(g.cpu().numpy(), 2 * d / n, rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("n,off", [(10007, 0), (4096, 1)])
+def test_adam_step_matches_formula(n, off):
+    """voge_adam_step against Adam's update written out in FP64 (Kingma & Ba,
+    Algorithm 1, bias-corrected), over three steps; the gradient is zeroed."""
+    voge = lib_ready()
+    rng = np.random.default_rng(23)
+    x0 = rng.standard_normal(n + off).astype(np.float32)
+    xd = to_dev(x0)
+    md, vd = torch.zeros(n + off, device="cuda"), torch.zeros(n + off, device="cuda")
+    xr, mr, vr = x0[off:].astype(np.float64), np.zeros(n), np.zeros(n)
+    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    for step in (1, 2, 3):
+        g = r32(rng.standard_normal(n + off))
+        gd = to_dev(g)
+        voge.voge_adam_step(xd[off:], gd[off:], md[off:], vd[off:], lr, step, b1, b2, eps)
+        gg = g[off:].astype(np.float64)
+        mr = b1 * mr + (1 - b1) * gg
+        vr = b2 * vr + (1 - b2) * gg * gg
+        xr = xr - lr * (mr / (1 - b1 ** step)) / (np.sqrt(vr / (1 - b2 ** step)) + eps)
+        torch.cuda.synchronize()
+        assert float(gd[off:].abs().max()) == 0.0
+    np.testing.assert_allclose(xd[off:].cpu().numpy(), xr, rtol=1e-5, atol=1e-6)
+
+
 def test_autograd_function_matches_direct_backward():
     voge = lib_ready()
     sc = scenes.fit_8x512(seed=18, N=300, B=1, side=32)
