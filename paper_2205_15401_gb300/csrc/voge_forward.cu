@@ -228,28 +228,72 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
         }
         if (__syncthreads_and(!active)) break;
     }
-    // sort the kept list by (l, index): candidates arrive nearly in depth
-    // order, so this insertion sort does little work
-    for (int i = 1; i < n; ++i) {
-        const float x = slk[i * NT + tid];
-        const int32_t y = sli[i * NT + tid];
-        int j = i - 1;
-        while (j >= 0) {
-            const float xj = slk[j * NT + tid];
-            const int32_t yj = sli[j * NT + tid];
-            if (!(xj > x || (xj == x && yj > y))) break;
-            slk[(j + 1) * NT + tid] = xj;
-            sli[(j + 1) * NT + tid] = yj;
-            --j;
-        }
-        slk[(j + 1) * NT + tid] = x;
-        sli[(j + 1) * NT + tid] = y;
-    }
+    // sort the kept list by (l, index).  Short lists (KM <= 20): in registers,
+    // entries at slots [KM - K, KM - K + n), the slots before them padded with
+    // (-inf, min) and after them with (+inf, max) so that they stay put;
+    // odd-even transposition sort, and since candidates arrive nearly in
+    // depth order the warp stops after a few passes, once no lane swapped in
+    // two passes.  Longer lists: insertion sort in the shared-memory columns.
     int32_t id[KM];
+    if constexpr (KM <= 20) {
+        float xk[KM];
 #pragma unroll
-    for (int s = 0; s < KM; ++s) {
-        const int k = s - (KM - K);
-        id[s] = (k >= 0 && k < n) ? sli[k * NT + tid] : -1;
+        for (int s = 0; s < KM; ++s) {
+            const int k = s - (KM - K);
+            const bool in = k >= 0 && k < n;
+            xk[s] = in ? slk[k * NT + tid] : (k < 0 ? -INFINITY : INFINITY);
+            id[s] = in ? sli[k * NT + tid] : (k < 0 ? INT32_MIN : INT32_MAX);
+        }
+        auto cmpx = [&](float& ka, int32_t& ia, float& kb, int32_t& ib) -> bool {
+            const bool gt = ka > kb || (ka == kb && ia > ib);
+            const float k0 = gt ? kb : ka, k1 = gt ? ka : kb;
+            const int32_t i0 = gt ? ib : ia, i1 = gt ? ia : ib;
+            ka = k0;
+            kb = k1;
+            ia = i0;
+            ib = i1;
+            return gt;
+        };
+        bool prev = true;
+        for (int pass = 0; pass < KM; ++pass) {
+            bool sw = false;
+            if (pass & 1) {
+#pragma unroll
+                for (int s = 1; s + 1 < KM; s += 2) sw |= cmpx(xk[s], id[s], xk[s + 1], id[s + 1]);
+            } else {
+#pragma unroll
+                for (int s = 0; s + 1 < KM; s += 2) sw |= cmpx(xk[s], id[s], xk[s + 1], id[s + 1]);
+            }
+            const bool any = __any_sync(0xffffffffu, sw);
+            if (!any && !prev) break;
+            prev = any;
+        }
+#pragma unroll
+        for (int s = 0; s < KM; ++s) {
+            const int k = s - (KM - K);
+            if (!(k >= 0 && k < n)) id[s] = -1;
+        }
+    } else {
+        for (int i = 1; i < n; ++i) {
+            const float x = slk[i * NT + tid];
+            const int32_t y = sli[i * NT + tid];
+            int j = i - 1;
+            while (j >= 0) {
+                const float xj = slk[j * NT + tid];
+                const int32_t yj = sli[j * NT + tid];
+                if (!(xj > x || (xj == x && yj > y))) break;
+                slk[(j + 1) * NT + tid] = xj;
+                sli[(j + 1) * NT + tid] = yj;
+                --j;
+            }
+            slk[(j + 1) * NT + tid] = x;
+            sli[(j + 1) * NT + tid] = y;
+        }
+#pragma unroll
+        for (int s = 0; s < KM; ++s) {
+            const int k = s - (KM - K);
+            id[s] = (k >= 0 && k < n) ? sli[k * NT + tid] : -1;
+        }
     }
     __syncthreads();  // selection buffers are free from here on
 
