@@ -39,32 +39,49 @@ int tile_grid(int KM, int fwd, int total_tiles);
 // Loss helper over a batch: per view, grad_image = 2 (image - target) / n and
 // loss += sum (image - target)^2 / n with n = H W C of that view.
 __global__ void __launch_bounds__(256) k_mse_batch(Args a) {
+    // One view after another; within a view the blocks stride over its
+    // image in 16-byte vectors (scalar when the view's arrays are not
+    // aligned), and each block adds its share of the view's loss once.
+    __shared__ float red[8];
     const int nv = a.hdr->nviews;
-    const int64_t total = a.hdr->total_elems;
-    const int lane = threadIdx.x & 31;
-    for (int64_t eb = (int64_t)blockIdx.x * blockDim.x; eb < total; eb += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = eb + threadIdx.x;
-        const bool live = e < total;
-        const int v = live ? view_of_elem(a.views, nv, e) : -1;
-        float sq = 0.0f;
-        float* loss = nullptr;
-        if (live) {
-            const ViewDesc& vd = a.views[v];
-            const int64_t x = e - vd.elem_base;
-            const float inv = 1.0f / (float)((int64_t)vd.H * vd.W * vd.C);
-            const float d = vd.image[x] - __ldg(vd.target + x);
-            const_cast<float*>(vd.grad_image)[x] = 2.0f * d * inv;
-            sq = d * d * inv;
-            loss = vd.loss;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int v = 0; v < nv; ++v) {
+        const ViewDesc& vd = a.views[v];
+        const int64_t n = (int64_t)vd.H * vd.W * vd.C;
+        const float inv = 1.0f / (float)n;
+        const float* x = vd.image;
+        const float* y = vd.target;
+        float* gx = const_cast<float*>(vd.grad_image);
+        float acc = 0.0f;
+        int64_t done = 0;
+        if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(gx)) & 15) == 0) {
+            const int64_t n4 = n >> 2;
+            for (int64_t q = first; q < n4; q += stride) {
+                const float4 p = reinterpret_cast<const float4*>(x)[q];
+                const float4 t = __ldg(reinterpret_cast<const float4*>(y) + q);
+                const float4 d = make_float4(p.x - t.x, p.y - t.y, p.z - t.z, p.w - t.w);
+                acc = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, acc))));
+                reinterpret_cast<float4*>(gx)[q] =
+                    make_float4(2.0f * d.x * inv, 2.0f * d.y * inv, 2.0f * d.z * inv, 2.0f * d.w * inv);
+            }
+            done = n4 << 2;
         }
-        const int v0 = __shfl_sync(0xffffffffu, v, 0);
-        float* l0 = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(loss), 0));
-        if (__all_sync(0xffffffffu, v == v0 || v < 0) && v0 >= 0) {
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0 && l0) atomicAdd(l0, sq);
-        } else if (loss) {
-            atomicAdd(loss, sq);
+        for (int64_t q = done + first; q < n; q += stride) {
+            const float d = x[q] - __ldg(y + q);
+            acc = fmaf(d, d, acc);
+            gx[q] = 2.0f * d * inv;
         }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) red[wid] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0 && vd.loss) {
+            float sum = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+            atomicAdd(vd.loss, sum * inv);
+        }
+        __syncthreads();  // red is reused by the next view
     }
 }
 }  // namespace voge
