@@ -13,6 +13,7 @@ Functions and the passages they follow:
   render_bwd               chain rule of Eq. 5-8 with frozen lists
   bbox                     exact conic bounding box of e^{q} > eta (App. A.3 role)
   quad_weights             exact outer integral of Eq. 1 by adaptive quadrature
+  sample                   neural sampler, Sec. 3.4 Eq. 10 (lists and weights -> per-kernel attributes)
 """
 from __future__ import annotations
 
@@ -57,6 +58,8 @@ def _load():
             P = ctypes.POINTER
             d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
             lib.vo_pose_to_RT.argtypes = [P(d), P(d), P(d)]
+            lib.vo_sample.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(i32), P(d), P(d), P(d), P(d)]
+            lib.vo_sample.restype = ctypes.c_int
             lib.vo_pose_grad.argtypes = [P(d), P(d), P(d)]
             lib.vo_trace_dir.argtypes = [P(d), P(d), P(d), P(d)]
             lib.vo_bbox.argtypes = [P(Camera), P(Params), P(d), P(d), P(i32)]
@@ -249,3 +252,21 @@ def quad_weights(l, a, b, tau):
     lib.vo_quad_weights(_ptr(l, ctypes.c_double), _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double),
                         int(l.shape[0]), float(tau), _ptr(out, ctypes.c_double))
     return out
+
+
+def sample(idx, weights, phi, N):
+    """Sec. 3.4 Eq. 10 on given lists: (alpha [N][C], wsum [N]) from idx [P][L]
+    (negative = empty), weights [P][L] and features phi [P][C]."""
+    lib = _load()
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    P, L = idx.shape
+    W = _f64(weights)
+    phi = _f64(phi)
+    C = phi.shape[1]
+    assert W.shape == (P, L) and phi.shape[0] == P
+    alpha = np.zeros((N, C))
+    wsum = np.zeros(N)
+    rc = lib.vo_sample(P, L, N, C, _ptr(idx, ctypes.c_int32), _ptr(W, ctypes.c_double), _ptr(phi, ctypes.c_double),
+                       _ptr(alpha, ctypes.c_double), _ptr(wsum, ctypes.c_double))
+    assert rc == 0
+    return alpha, wsum

@@ -20,7 +20,10 @@
  *   - weights and blend, Eq. 8 (W_k = T(l_k) e^{q_k}, C = sum W_k c_k);
  *   - backward: the chain rule of the steps above with the lists frozen;
  *   - the exact outer integral of Eq. 1 by adaptive quadrature (to bound the
- *     approximation of Eq. 8; App. A.2, Fig. 6).
+ *     approximation of Eq. 8; App. A.2, Fig. 6);
+ *   - the neural sampler, Sec. 3.4 Eq. 10: alpha_k = sum_p W_pk phi_p /
+ *     sum_p W_pk over the pixels whose kept list holds k (W_pk = 0
+ *     elsewhere); a kernel no pixel keeps gets alpha_k = 0.
  * Notation: a = e^{q} is the peak density on the ray, qt = -2q >= 0,
  * b = DᵀPD = 1/sigma^2, m = a/2 so that tau*sum m(1+erf) is Eq. 7's exponent.
  *
@@ -629,4 +632,27 @@ void vo_quad_weights(const double* l, const double* a, const double* b, int n, d
         }
         W_exact[k] = acc;
     }
+}
+
+/* Neural sampler, Sec. 3.4 Eq. 10, on given per-pixel lists and weights:
+ * idx [P][L] (negative = empty slot), W [P][L], phi [P][C] ->
+ * alpha [N][C] = sum_p W_pk phi_p / sum_p W_pk and wsum [N] = sum_p W_pk
+ * (alpha_k = 0 where wsum_k = 0).  Plain loops in pixel order. */
+int vo_sample(int64_t P, int L, int N, int C, const int32_t* idx, const double* W, const double* phi, double* alpha,
+              double* wsum) {
+    if (P < 0 || L < 0 || N < 0 || C < 0) return -1;
+    memset(alpha, 0, sizeof(double) * (size_t)N * (size_t)C);
+    memset(wsum, 0, sizeof(double) * (size_t)N);
+    for (int64_t p = 0; p < P; ++p) {
+        for (int k = 0; k < L; ++k) {
+            const int32_t g = idx[p * L + k];
+            if (g < 0 || g >= N) continue;
+            const double w = W[p * L + k];
+            wsum[g] += w;
+            for (int c = 0; c < C; ++c) alpha[(int64_t)g * C + c] += w * phi[p * C + c];
+        }
+    }
+    for (int g = 0; g < N; ++g)
+        for (int c = 0; c < C; ++c) alpha[(int64_t)g * C + c] = wsum[g] > 0.0 ? alpha[(int64_t)g * C + c] / wsum[g] : 0.0;
+    return 0;
 }
