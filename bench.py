@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--no-sampler", action="store_true")
     return ap.parse_args()
 
 
@@ -189,6 +190,45 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- serving ---
+def sampler_bench(voge, index, weights, N, dev, reps=10):
+    """voge_sample on the step's own lists and weights with synthetic features
+    of 3 (texture) and 128 (deep features) channels: device time per call and
+    the algorithmic bytes (lists, weights and features read once, the
+    per-kernel rows written and normalised) against the measured HBM peak."""
+    import torch
+
+    P, L = index.shape
+    peak = measured_hbm_gbs()
+    out = {"workload": f"lists and weights of the fit_8x512 forward ({P} pixels, L={L}, N={N}); features N(0,1)"}
+    for C in (3, 128):
+        g = torch.Generator(device=dev).manual_seed(C)
+        phi = torch.randn((P, C), device=dev, generator=g)
+        alpha = torch.empty((N, C), device=dev)
+        wsum = torch.empty((N,), device=dev)
+        for _ in range(3):
+            voge.voge_sample(index, weights, phi, N, alpha, wsum)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            voge.voge_sample(index, weights, phi, N, alpha, wsum)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = P * L * 8 + P * C * 4 + N * (C + 1) * 4 * 3
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[f"C{C}"] = {"ms": ms, "mpix_s": P / (ms / 1e3) / 1e6, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                        "hbm_peak_gbs": peak, "frac": gbs / peak if peak else None}
+    return out
+
+
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
     """Poisson render-and-compare requests (mean gap 2 ms) against resident scenes.
 
@@ -497,6 +537,11 @@ def main():
                                "(resident scenes), side {128,256,512}, C {3,16,128}, K {10,20,32}",
                    "batched": batched, "plain": plain_srv}
 
+    # ------------------------------------------------ neural sampler (Sec. 3.4 Eq. 10)
+    sampler = None
+    if not args.no_sampler:
+        sampler = sampler_bench(voge, index[:, : r.L].contiguous(), weights[:, : r.L].contiguous(), N, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -513,7 +558,7 @@ def main():
                           **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
                           "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
-               "serving": serving,
+               "serving": serving, "sampler": sampler,
                "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:

@@ -167,6 +167,30 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
                       size_t workspace_bytes, voge_stream_t stream);
 
 /*
+ * Neural sampler of Sec. 3.4 (Eq. 10): per-kernel attributes from per-pixel
+ * features (image values, deep features) through the renderer's kept lists,
+ *   alpha_k = sum_p W_pk phi_p / sum_p W_pk,
+ * the sums over the pixels whose list holds k (W_pk of Eq. 8 is zero for the
+ * others).  A kernel that no pixel keeps gets alpha_k = 0.
+ *
+ *   pixels    number of pixels P (all views of a voge_render_fwd call: the
+ *             sum of H*W)
+ *   L         list length of `index` and `weights` (voge_list_length)
+ *   N, C      kernels and feature channels
+ *   index     device, [P][L] int32 from voge_render_fwd (negative = empty
+ *             slot; indices >= N are ignored)
+ *   weights   device, [P][L] float from voge_render_fwd
+ *   features  device, [P][C] float: phi_p
+ *   alpha     device, [N][C] float, written (overwritten, not accumulated)
+ *   wsum      device, [N] float, written: sum_p W_pk
+ *   Asynchronous on `stream`; allocates nothing.  VOGE_ERR_ARG for negative
+ *   sizes, C < 1 or a missing pointer.  Floating-point atomics make the last
+ *   bits depend on scheduling.
+ */
+int voge_sample(int64_t pixels, int32_t L, int32_t N, int32_t C, const int32_t* index, const float* weights,
+                const float* features, float* alpha, float* wsum, voge_stream_t stream);
+
+/*
  * Camera pose (azimuth, elevation, distance, roll), radians -> R, T (host).
  * Look-at camera: centre dist*(cos e sin a, sin e, cos e cos a), looking at
  * the world origin, world up +y, then a roll about the optical axis.  The

@@ -69,6 +69,9 @@ def lib():
             L.voge_render_bwd_w.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                             vp, ctypes.c_size_t, vp]
             L.voge_render_bwd_w.restype = ctypes.c_int
+            L.voge_sample.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp,
+                                      vp]
+            L.voge_sample.restype = ctypes.c_int
             L.voge_pose_to_RT.argtypes = [P(ctypes.c_double), P(ctypes.c_float), P(ctypes.c_float)]
             L.voge_pose_to_RT.restype = None
             L.voge_pose_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
@@ -175,6 +178,22 @@ def voge_render_bwd_w(cams, params, means, inv_cov, attr, index, weights, grad_i
                                  _ptr(grad_inv_cov, f32), _ptr(grad_attr, f32), _ptr(grad_cam, f32),
                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "voge_render_bwd_w")
+
+
+def voge_sample(index, weights, features, N, alpha=None, wsum=None, stream=None):
+    """Neural sampler (Sec. 3.4 Eq. 10): (alpha [N][C], wsum [N]) from the
+    renderer's index [P][L] / weights [P][L] and per-pixel features [P][C]."""
+    f32, i32 = torch.float32, torch.int32
+    P, L = index.shape
+    C = features.shape[1]
+    if alpha is None:
+        alpha = torch.empty((N, C), dtype=f32, device=features.device)
+    if wsum is None:
+        wsum = torch.empty((N,), dtype=f32, device=features.device)
+    rc = lib().voge_sample(P, L, N, C, _ptr(index, i32), _ptr(weights, f32), _ptr(features, f32), _ptr(alpha, f32),
+                           _ptr(wsum, f32), _stream(stream))
+    _check(rc, "voge_sample")
+    return alpha, wsum
 
 
 def voge_render_fwd_static(cams, params, means, inv_cov, attr, image, weights, index, stream=None):
