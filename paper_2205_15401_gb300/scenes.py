@@ -135,6 +135,32 @@ def large_1024(seed=0, N=500_000, C=16):
             "tau": 1.0, "K": 32, "eta": 1e-4}
 
 
+def two_cuboids(gap, occludee_shift=(0.0, 0.0, 0.0), side=128, n=6):
+    """Occlusion-reasoning scene (the two-cuboid setup of Sec. 4): a red
+    occluder 1 x 1 x 0.6 scale units centred on the optical axis at depth 6,
+    and a blue 1 x 1 x 1 occludee `gap` units behind it, moved by
+    `occludee_shift`.  Each cuboid is an n x n x m grid of axis-aligned
+    Gaussians spaced like its cells.  Returns the scene dict with "parts":
+    index ranges of the occluder and the occludee."""
+    def box(centre, size, m):
+        axes = [np.linspace(-0.5, 0.5, k) * sz for k, sz in zip((n, n, m), size)]
+        g = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3) + np.asarray(centre)
+        s = np.array([sz / k for sz, k in zip(size, (n, n, m))]) * 0.6
+        return g, np.tile(s, (g.shape[0], 1))
+    a_m, a_s = box((0.0, 0.0, 6.0), (1.0, 1.0, 0.6), 3)
+    b_c = np.array([0.0, 0.0, 6.0 + 0.3 + gap + 0.5]) + np.asarray(occludee_shift, dtype=np.float64)
+    b_m, b_s = box(b_c, (1.0, 1.0, 1.0), n)
+    means = np.concatenate([a_m, b_m]).astype(np.float32)
+    scales = np.concatenate([a_s, b_s])
+    rot = np.tile(np.eye(3), (means.shape[0], 1, 1))
+    attr = np.concatenate([np.tile([1.0, 0.0, 0.0], (a_m.shape[0], 1)), np.tile([0.0, 0.0, 1.0], (b_m.shape[0], 1))])
+    na = a_m.shape[0]
+    return {"name": "two_cuboids", "means": means, "inv_cov": inverse_covariance(rot, scales),
+            "attr": attr.astype(np.float32), "cameras": [_identity_camera(side, side, side)], "poses": None,
+            "H": side, "W": side, "F": float(side), "tau": 1.0, "K": 32, "eta": 1e-3,
+            "parts": {"occluder": (0, na), "occludee": (na, means.shape[0])}}
+
+
 def serving_stream(seed=0, duration_s=10.0, mean_gap_s=0.002):
     """Request descriptors for the Poisson serving workload."""
     rng = np.random.default_rng(seed)
