@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--no-sampler", action="store_true")
+    ap.add_argument("--no-posefit", action="store_true")
     return ap.parse_args()
 
 
@@ -220,6 +221,44 @@ def sampler_bench(voge, index, weights, N, dev, reps=10):
         out[f"C{C}"] = {"ms": ms, "mpix_s": P / (ms / 1e3) / 1e6, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
                         "hbm_peak_gbs": peak, "frac": gbs / peak if peak else None}
     return out
+
+
+def posefit_bench(voge, dev, steps=20, warmup=3):
+    """Feature-level pose fitting at the scale of Sec. 4.1's render-and-compare
+    loop: 144 start poses (12 azimuths x 4 elevations x 3 rolls) of the
+    posefit_256 object (N = 4000, 128-channel features, 256 x 256) fitted as
+    one batch; device time per fitting step of all starts."""
+    import torch
+
+    from paper_2205_15401_gb300 import scenes
+    from paper_2205_15401_gb300.posefit import PoseFitter
+
+    sc = scenes.posefit_256(seed=0)
+    side, C = 256, sc["attr"].shape[1]
+    true = sc["poses"][0]
+    m, p, a = (torch.tensor(sc[k], device=dev) for k in ("means", "inv_cov", "attr"))
+    R, T = voge.voge_pose_to_RT(true)
+    cam = {"R": R, "T": T, "F": float(side), "Ox": side / 2, "Oy": side / 2, "H": side, "W": side}
+    target = voge.Renderer([cam], m.shape[0], C, K=20, tau=1.0, thresh=1e-3, device=dev).forward(m, p, a)[0].clone()
+    starts = np.array([[az, el, true[2], ro] for az in np.linspace(-np.pi, np.pi, 12, endpoint=False)
+                       for el in (-0.2, 0.1, 0.4, 0.7) for ro in (-0.1, 0.0, 0.1)])
+    fitter = PoseFitter(m, p, a, target, side, side, float(side), starts, lr=0.02, device=dev)
+    for _ in range(warmup):
+        fitter.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(steps):
+        fitter.step()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "posefit_256: N=4000, C=128 features, 256x256, K=20; 144 start poses fitted as one batch "
+                        "(forward + MSE + backward to the cameras + pose chain + Adam per step)",
+            "starts": len(starts), "ms_per_step": ms, "start_steps_per_s": len(starts) / (ms / 1e3),
+            "mpix_s": len(starts) * side * side / (ms / 1e3) / 1e6, "wall_ms_per_step": 1e3 * wall / steps}
 
 
 def measured_hbm_gbs():
@@ -542,6 +581,10 @@ def main():
     if not args.no_sampler:
         sampler = sampler_bench(voge, index[:, : r.L].contiguous(), weights[:, : r.L].contiguous(), N, dev)
 
+    posefit = None
+    if not args.no_posefit:
+        posefit = posefit_bench(voge, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -558,7 +601,7 @@ def main():
                           **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
                           "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
-               "serving": serving, "sampler": sampler,
+               "serving": serving, "sampler": sampler, "posefit": posefit,
                "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:
