@@ -14,6 +14,8 @@ Functions and the passages they follow:
   bbox                     exact conic bounding box of e^{q} > eta (App. A.3 role)
   quad_weights             exact outer integral of Eq. 1 by adaptive quadrature
   sample                   neural sampler, Sec. 3.4 Eq. 10 (lists and weights -> per-kernel attributes)
+  mesh_to_gaussians        mesh converter of App. A.4: isotropic, optionally flattened along normals
+  points_to_gaussians      point-cloud converter of App. A.4 (the same sigma from the m nearest points)
 """
 from __future__ import annotations
 
@@ -270,3 +272,68 @@ def sample(idx, weights, phi, N):
                        _ptr(alpha, ctypes.c_double), _ptr(wsum, ctypes.c_double))
     assert rc == 0
     return alpha, wsum
+
+
+def _iso_sigma(d, zeta):
+    """App. A.4: sigma_k = (d_k / 2)^2 / log(1 / zeta), the variance on the
+    diagonal of the isotropic Sigma_k."""
+    return (np.asarray(d, np.float64) / 2.0) ** 2 / np.log(1.0 / zeta)
+
+
+def _pack_inverse(Pm):
+    """[n][3][3] symmetric -> [n][6] (xx, xy, xz, yy, yz, zz)."""
+    return np.stack([Pm[:, 0, 0], Pm[:, 0, 1], Pm[:, 0, 2], Pm[:, 1, 1], Pm[:, 1, 2], Pm[:, 2, 2]], 1)
+
+
+def mesh_to_gaussians(verts, faces, zeta=0.5, flatten=None):
+    """Mesh converter (App. A.4): one Gaussian per vertex; d_k is the mean
+    length of the distinct edges at vertex k; Sigma_k = sigma_k I.
+    With `flatten` = f (the variant App. B describes), the Gaussian is
+    flattened along the vertex normal (the normalised sum of the adjacent
+    faces' area-weighted normals):
+    Sigma_k = sigma_k (I - n nᵀ) + f sigma_k n nᵀ.  Returns (means [V][3],
+    inv_cov [V][6]) in FP64; a vertex on no edge has no d_k and gets an
+    inverse covariance of nan."""
+    V = np.asarray(verts, np.float64)
+    Fc = np.asarray(faces, np.int64)
+    edges = set()
+    for a, b, c in Fc:
+        for i, j in ((a, b), (b, c), (c, a)):
+            edges.add((min(i, j), max(i, j)))
+    total = np.zeros(len(V))
+    count = np.zeros(len(V))
+    for i, j in sorted(edges):
+        length = np.linalg.norm(V[i] - V[j])
+        total[i] += length
+        total[j] += length
+        count[i] += 1
+        count[j] += 1
+    d = np.where(count > 0, total / np.where(count > 0, count, 1), np.nan)
+    sig = _iso_sigma(d, zeta)
+    Pm = np.tile(np.eye(3), (len(V), 1, 1)) / sig[:, None, None]
+    if flatten is not None:
+        nrm = np.zeros_like(V)
+        for a, b, c in Fc:
+            fn = np.cross(V[b] - V[a], V[c] - V[a])  # length = twice the area
+            nrm[a] += fn
+            nrm[b] += fn
+            nrm[c] += fn
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        nn = nrm[:, :, None] * nrm[:, None, :]
+        Pm = (np.eye(3)[None] - nn) / sig[:, None, None] + nn / (flatten * sig[:, None, None])
+    return V.copy(), _pack_inverse(Pm)
+
+
+def points_to_gaussians(points, m=4, zeta=0.5):
+    """Point-cloud converter (App. A.4): the same sigma_k with d_k the mean
+    distance from point k to its m nearest other points (brute force)."""
+    X = np.asarray(points, np.float64)
+    n = len(X)
+    d = np.zeros(n)
+    for k in range(n):
+        dist = np.sqrt(((X - X[k]) ** 2).sum(1))
+        dist[k] = np.inf
+        d[k] = np.sort(dist)[:m].mean()
+    sig = _iso_sigma(d, zeta)
+    Pm = np.tile(np.eye(3), (n, 1, 1)) / sig[:, None, None]
+    return X.copy(), _pack_inverse(Pm)
