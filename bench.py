@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-posefit", action="store_true")
+    ap.add_argument("--no-converters", action="store_true")
     return ap.parse_args()
 
 
@@ -259,6 +260,33 @@ def posefit_bench(voge, dev, steps=20, warmup=3):
                         "(forward + MSE + backward to the cameras + pose chain + Adam per step)",
             "starts": len(starts), "ms_per_step": ms, "start_steps_per_s": len(starts) / (ms / 1e3),
             "mpix_s": len(starts) * side * side / (ms / 1e3) / 1e6, "wall_ms_per_step": 1e3 * wall / steps}
+
+
+def converters_bench(voge, dev, reps=5):
+    """Mesh converter on a 400 x 800 UV sphere (320k vertices, 640k faces) and
+    point-cloud converter on 50k points with m = 8 (App. A.4): device ms per call."""
+    import torch
+
+    from paper_2205_15401_gb300 import scenes
+
+    V, F = scenes.uv_sphere(400, 800, 1.0, seed=0, jitter=0.01)
+    Vd, Fd = torch.tensor(V, device=dev), torch.tensor(F, device=dev)
+    X = torch.tensor(np.random.default_rng(0).uniform(-1, 1, (50_000, 3)).astype(np.float32), device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    return {"mesh": {"vertices": int(V.shape[0]), "faces": int(F.shape[0]), "flatten": 0.3,
+                     "ms": timed(lambda: voge.voge_mesh_to_gaussians(Vd, Fd, 0.5, 0.3))},
+            "points": {"points": int(X.shape[0]), "m": 8, "ms": timed(lambda: voge.voge_points_to_gaussians(X, 8, 0.5))}}
 
 
 def measured_hbm_gbs():
@@ -581,6 +609,10 @@ def main():
     if not args.no_sampler:
         sampler = sampler_bench(voge, index[:, : r.L].contiguous(), weights[:, : r.L].contiguous(), N, dev)
 
+    converters = None
+    if not args.no_converters:
+        converters = converters_bench(voge, dev)
+
     posefit = None
     if not args.no_posefit:
         posefit = posefit_bench(voge, dev)
@@ -601,7 +633,7 @@ def main():
                           **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
                           "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
-               "serving": serving, "sampler": sampler, "posefit": posefit,
+               "serving": serving, "sampler": sampler, "posefit": posefit, "converters": converters,
                "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:

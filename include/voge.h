@@ -191,6 +191,35 @@ int voge_sample(int64_t pixels, int32_t L, int32_t N, int32_t C, const int32_t* 
                 const float* features, float* alpha, float* wsum, voge_stream_t stream);
 
 /*
+ * Mesh and point-cloud converters (App. A.4): one isotropic Gaussian per
+ * vertex or point, centred on it, with the variance on the diagonal
+ *   sigma_k = (d_k / 2)^2 / log(1 / zeta),
+ * zeta in (0, 1) the coverage rate (0.5 standard).  Outputs are the renderer's
+ * inputs: means [V][3] and inverse covariances [V][6] (xx, xy, xz, yy, yz, zz),
+ * device float, written.  Asynchronous on `stream`.
+ *
+ * Mesh: d_k is the mean length of the distinct edges at vertex k.
+ *   verts  device, [V][3] float;  faces  device, [F][3] int32 vertex indices
+ *          (faces with an index outside [0, V) or a repeated vertex are
+ *          skipped; a vertex on no edge gets NaN inverse covariances).
+ *   flatten  0: isotropic.  f > 0: flattened along the vertex normal n (the
+ *          normalised sum of the adjacent faces' area-weighted normals), the
+ *          variant App. B describes: Sigma = sigma (I - n nᵀ) + f sigma n nᵀ.
+ *   workspace  device, >= voge_mesh_workspace_bytes(V, F), 256-byte aligned
+ *          (an edge set and per-vertex sums); VOGE_ERR_WORKSPACE otherwise.
+ * Points: d_k is the mean distance from point k to its m nearest other
+ *   points, 1 <= m <= 32 and m < V (brute force over all points).
+ * VOGE_ERR_ARG for negative sizes, zeta outside (0, 1), a negative flatten,
+ * m out of range or a missing pointer.
+ */
+size_t voge_mesh_workspace_bytes(int32_t V, int32_t F);
+int voge_mesh_to_gaussians(int32_t V, int32_t F, const float* verts, const int32_t* faces, float zeta, float flatten,
+                           float* means, float* inv_cov, void* workspace, size_t workspace_bytes,
+                           voge_stream_t stream);
+int voge_points_to_gaussians(int32_t V, int32_t m, float zeta, const float* points, float* means, float* inv_cov,
+                             voge_stream_t stream);
+
+/*
  * Camera pose (azimuth, elevation, distance, roll), radians -> R, T (host).
  * Look-at camera: centre dist*(cos e sin a, sin e, cos e cos a), looking at
  * the world origin, world up +y, then a roll about the optical axis.  The

@@ -161,6 +161,30 @@ def two_cuboids(gap, occludee_shift=(0.0, 0.0, 0.0), side=128, n=6):
             "parts": {"occluder": (0, na), "occludee": (na, means.shape[0])}}
 
 
+def uv_sphere(n_lat=12, n_lon=24, radius=1.0, seed=None, jitter=0.0):
+    """Triangle mesh of a sphere: poles plus n_lat - 1 rings of n_lon vertices
+    (float32 vertices, int32 faces); `jitter` moves the vertices radially."""
+    verts = [[0.0, 0.0, radius]]
+    for i in range(1, n_lat):
+        th = math.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2 * math.pi * j / n_lon
+            verts.append([radius * math.sin(th) * math.cos(ph), radius * math.sin(th) * math.sin(ph),
+                          radius * math.cos(th)])
+    verts.append([0.0, 0.0, -radius])
+    verts = np.array(verts)
+    if jitter > 0:
+        verts *= 1.0 + jitter * np.random.default_rng(seed).uniform(-1, 1, (len(verts), 1))
+    ring = lambda i, j: 1 + (i - 1) * n_lon + (j % n_lon)
+    last = len(verts) - 1
+    faces = [[0, ring(1, j), ring(1, j + 1)] for j in range(n_lon)]
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            faces += [[ring(i, j), ring(i + 1, j), ring(i + 1, j + 1)], [ring(i, j), ring(i + 1, j + 1), ring(i, j + 1)]]
+    faces += [[ring(n_lat - 1, j), last, ring(n_lat - 1, j + 1)] for j in range(n_lon)]
+    return verts.astype(np.float32), np.array(faces, np.int32)
+
+
 def serving_stream(seed=0, duration_s=10.0, mean_gap_s=0.002):
     """Request descriptors for the Poisson serving workload."""
     rng = np.random.default_rng(seed)

@@ -72,6 +72,13 @@ def lib():
             L.voge_sample.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp,
                                       vp]
             L.voge_sample.restype = ctypes.c_int
+            L.voge_mesh_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+            L.voge_mesh_workspace_bytes.restype = ctypes.c_size_t
+            L.voge_mesh_to_gaussians.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp, ctypes.c_float,
+                                                 ctypes.c_float, vp, vp, vp, ctypes.c_size_t, vp]
+            L.voge_mesh_to_gaussians.restype = ctypes.c_int
+            L.voge_points_to_gaussians.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp, vp, vp, vp]
+            L.voge_points_to_gaussians.restype = ctypes.c_int
             L.voge_pose_to_RT.argtypes = [P(ctypes.c_double), P(ctypes.c_float), P(ctypes.c_float)]
             L.voge_pose_to_RT.restype = None
             L.voge_pose_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
@@ -194,6 +201,31 @@ def voge_sample(index, weights, features, N, alpha=None, wsum=None, stream=None)
                            _ptr(wsum, f32), _stream(stream))
     _check(rc, "voge_sample")
     return alpha, wsum
+
+
+def voge_mesh_to_gaussians(verts, faces, zeta=0.5, flatten=0.0, stream=None):
+    """Mesh converter (App. A.4): (means [V][3], inv_cov [V][6]) on the device."""
+    f32, i32 = torch.float32, torch.int32
+    V, F = verts.shape[0], faces.shape[0]
+    means = torch.empty((V, 3), dtype=f32, device=verts.device)
+    inv_cov = torch.empty((V, 6), dtype=f32, device=verts.device)
+    nbytes = lib().voge_mesh_workspace_bytes(V, F)
+    ws = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=verts.device)
+    _check(lib().voge_mesh_to_gaussians(V, F, _ptr(verts, f32), _ptr(faces, i32), float(zeta), float(flatten),
+                                        _ptr(means, f32), _ptr(inv_cov, f32), _ptr(ws), ws.numel(), _stream(stream)),
+           "voge_mesh_to_gaussians")
+    return means, inv_cov
+
+
+def voge_points_to_gaussians(points, m=4, zeta=0.5, stream=None):
+    """Point-cloud converter (App. A.4): (means [V][3], inv_cov [V][6]) on the device."""
+    f32 = torch.float32
+    V = points.shape[0]
+    means = torch.empty((V, 3), dtype=f32, device=points.device)
+    inv_cov = torch.empty((V, 6), dtype=f32, device=points.device)
+    _check(lib().voge_points_to_gaussians(V, int(m), float(zeta), _ptr(points, f32), _ptr(means, f32),
+                                          _ptr(inv_cov, f32), _stream(stream)), "voge_points_to_gaussians")
+    return means, inv_cov
 
 
 def voge_render_fwd_static(cams, params, means, inv_cov, attr, image, weights, index, stream=None):
