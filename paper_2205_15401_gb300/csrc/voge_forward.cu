@@ -176,7 +176,6 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             //    candidates at the same time instead of the union of all hits.
             //    One cursor runs over all mask words, so the warp iterates as
             //    often as its busiest lane has hits in the chunk.
-            const float* lmin = reinterpret_cast<const float*>(stage + 3 * NT) + 3;
             int w = 0;
             uint32_t m = smask[tid];
             for (;;) {
@@ -184,11 +183,12 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 if (m == 0) break;
                 const int q = w * 32 + __ffs(m) - 1;
                 m &= m - 1;
-                if (src.mode == 1 && lmin[4 * q] > kmax) {
+                const float4 r3 = stage[3 * NT + q];  // .w: the candidate's depth lower bound
+                if (src.mode == 1 && r3.w > kmax) {
                     active = false;  // sorted by lower bound: nothing later can enter
                     break;
                 }
-                const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q], r3 = stage[3 * NT + q];
+                const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q];
                 const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
                 if (l > 0.0f) {
                     const int32_t g = sgid[q];
