@@ -33,6 +33,15 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpix/s fwd+bwd (50k Gaussians, 512², K=20) vs plain; serving p50/p99 ms"
 UNIT = "Mpix/s"
 WORKLOAD = dict(views=8, side=512, N=50_000, K=20, eta=0.01, C=3, tau=1.0)
+
+
+def workload_config(world=1):
+    """The `config` of both arms: the workload, not the sample an arm times."""
+    return {"workload": "fit_8x512: 8 views 512x512, N=50,000 anisotropic Gaussians, K=20, eta=0.01, RGB; "
+                        "step = forward + MSE + backward + Adam",
+            **WORKLOAD, "pixels_per_step": WORKLOAD["views"] * WORKLOAD["side"] ** 2,
+            "parallelism": f"replicas x{world}",
+            "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"}
 # Algorithmic FP32 work of the fine pass (Eq. 7-8) per (k, j) pair of a pixel's
 # kept list, counting an FMA as 2 FLOP:
 #   forward  24 = depth difference of two-float l (3) + scale (1) + A&S 7.1.28
@@ -185,7 +194,7 @@ def run_reference(args):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic",
-                      "config": {"workload": "fit_8x512 (oracle sample)", **WORKLOAD, "pixels_per_step": n},
+                      "config": workload_config(1),
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -628,10 +637,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": "fit_8x512: 8 views 512x512, N=50,000 anisotropic Gaussians, K=20, "
-                                      "eta=0.01, RGB; step = forward + MSE + backward + Adam",
-                          **W, "pixels_per_step": P, "parallelism": f"replicas x{world}",
-                          "l2": "each step writes 0.34 GB of weights/index lists (> 126 MB L2)"},
+               "config": workload_config(world),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
                "serving": serving, "sampler": sampler, "posefit": posefit, "converters": converters,
                "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
