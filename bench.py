@@ -52,9 +52,14 @@ def workload_config(world=1):
 #             timed step hands the forward's weights to the backward
 #             (voge_render_bwd_w), so the forward pair is not recomputed
 #             (it would add 24)
-# plus, per kept entry, 80 FLOP for the chain to camera space (backward only).
+# plus, per kept entry, 80 FLOP for the chain to camera space (backward only)
+# and, in the forward, 30 FLOP for the entry's coarse-pass ray trace (Eq. 6:
+# offsets 4, b and its numerator 11, qb 5, the threshold test 1, l 5) and its
+# fine-pass sigma and e^{q} (4).  Candidates the coarse pass traces and
+# rejects are not counted, so the forward figure is a lower bound.
 FLOP_PER_PAIR = {"fwd": 24, "bwd": 28}
 FLOP_PER_ENTRY_BWD = 80
+FLOP_PER_ENTRY_FWD = 30
 # GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -526,7 +531,7 @@ def main():
         if top_name.startswith("k_backward"):
             flop = pairs * FLOP_PER_PAIR["bwd"] + entries * FLOP_PER_ENTRY_BWD
         elif top_name.startswith("k_render"):
-            flop = pairs * FLOP_PER_PAIR["fwd"]
+            flop = pairs * FLOP_PER_PAIR["fwd"] + entries * FLOP_PER_ENTRY_FWD
         else:
             flop = None
         if flop is not None:
