@@ -326,13 +326,13 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
 }
 
 // Backward tiles are 16 x TH (TH = 8): each binning tile of tile_h rows is
-// split into tile_h / TH of them, so a CTA of 128 threads keeps more
-// registers per thread and less shared memory (more L1) than one per
-// binning tile.  WIDE kernels take the views with C >= 8 (warp-cooperative
+// split into tile_h / TH of them, so CTAs of 128 threads use less shared
+// memory each (more L1) than one per binning tile; lists of up to 20 entries
+// run four CTAs per SM, longer ones three with more registers.  WIDE kernels take the views with C >= 8 (warp-cooperative
 // attribute rows), the others the rest; they are separate kernels so that
 // each gets its own register allocation.  Each skips the other's tiles.
 template <int KM, int TH, bool WIDE>
-__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : 3) k_backward(Args a) {
+__global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : (KM <= 20 ? 4 : 3)) k_backward(Args a) {
     __shared__ int s_slot;
     // every view of one class launch has the same tile height (a serving tick
     // mixes classes, so take it from this class's first tile)
