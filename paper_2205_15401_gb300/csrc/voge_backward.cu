@@ -1,7 +1,8 @@
 // voge_backward.cu -- adjoint of the forward pass with the kept lists frozen.
 //
-// Only the per-pixel index lists come from the forward pass; l, e^{q},
-// sigma, T(l_k) and every erf term of Eq. 7 are recomputed here.  For a pixel
+// The per-pixel index lists come from the forward pass, and its weights W_k
+// when the caller passes them (voge_render_bwd_w); l, e^{q}, sigma, every erf
+// term of Eq. 7 and, without the weights, T(l_k) are recomputed here.  For a pixel
 // with list L_p and upstream gradient g_p = dLoss/dimage_p:
 //   dc_k += W_k g_p,  G_k = g_p . c_k,  dA_k = -tau G_k W_k
 //   dm_j += dA_k (1 + erf u_kj),  du_kj = dA_k m_j (2/sqrt(pi)) e^{-u_kj^2}
@@ -13,7 +14,8 @@
 //   dP_ab += dqt V_a V_b + dl (V_a D_b + D_a V_b) / (2b) + db D_a D_b,
 // with V = M - l D (App. A.1: VᵀPD = 0, so l's own dependence drops out of qt).
 // Camera-space sums per (view, Gaussian) are rotated to world space and
-// reduced into the camera pose by k_grad_finalize.
+// reduced into the camera pose by the finalize kernels at the end of this
+// file.
 #include "voge_device.cuh"
 #include "voge_trace.cuh"
 

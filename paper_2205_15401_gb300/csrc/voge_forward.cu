@@ -1,11 +1,13 @@
-// voge_forward.cu -- fused coarse + fine forward pass, one CTA per tile of
-// 16 x TH pixels, one thread per pixel.
+// voge_forward.cu -- fused coarse + fine forward pass: persistent CTAs over
+// tiles of 16 x TH pixels, one thread per pixel.
 //
-// Coarse pass (Sec. 3.3, App. A.3): the tile's candidate Gaussians are staged
-// in shared memory in chunks; every pixel traces each of them (Eq. 6), keeps
-// those with e^{q} > eta and l > 0, and holds the K nearest by (l, index) in
-// a register list.  When eta > 0 the candidates are first sorted by a lower
-// bound of l, so a pixel stops as soon as no later candidate can enter.
+// Coarse pass (Sec. 3.3, App. A.3): the tile's candidate Gaussians (binned
+// and, when eta > 0, sorted by a lower bound of l by k_sort_tiles) are staged
+// in shared memory in chunks of 16 TH.  While staging, each candidate's
+// threshold conic gives a 16-bit pixel mask per tile row; every pixel traces
+// (Eq. 6) only the candidates whose mask covers it, keeps those with
+// e^{q} > eta and l > 0, and holds the K nearest by (l, index) in its own
+// shared-memory column.  A pixel stops once no later candidate can enter.
 //
 // Fine pass (Eq. 7-8): with the kept list L_p,
 //   A_k = sum_{j in L_p} (a_j/2)(1 + erf((l_k - l_j) sqrt(b_j/2))),
@@ -20,7 +22,7 @@ namespace voge {
 
 // Candidate source of one tile.
 struct TileSrc {
-    int mode;          // 0 = binned list in global, 1 = sorted list in smem, 2 = every Gaussian (plain/overflow)
+    int mode;          // 0 = binned list, 1 = binned list sorted by depth bound, 2 = every Gaussian (plain/overflow)
     int filter_box;    // mode 2: test the Gaussian's tile box
     int count;
     int start;

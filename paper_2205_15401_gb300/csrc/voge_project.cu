@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(256) k_scatter(Args a) {
 }
 
 // Depth order of each tile's candidate list (ascending lower bound of l), so
-// that a pixel can stop once no later candidate can enter its list.  One warp
-// per tile, bitonic sort in the warp's shared memory (lists of at most
-// kSortMax entries; longer lists stay unsorted and are traced in full).
+// that a pixel can stop once no later candidate can enter its list.  Lists of
+// at most kSortMax entries are sorted (one CTA per list, below); longer lists
+// stay unsorted and are traced in full.
 __device__ __forceinline__ bool tile_sorted(int use_thresh, int plain, int cnt, int64_t off, int64_t cap) {
     return use_thresh && !plain && cnt > 1 && cnt <= kSortMax && off + cnt <= cap;
 }
