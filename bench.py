@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-posefit", action="store_true")
     ap.add_argument("--no-converters", action="store_true")
+    ap.add_argument("--no-alu-ceilings", action="store_true", help="skip the measured ALU ceilings")
     return ap.parse_args()
 
 
@@ -407,10 +408,16 @@ def reduce_over_ranks(ms, pixels, world, device):
     return float(t.item()), float(p.item())
 
 
+# The sources that define the step's kernels and their launches: the committed
+# DRAM traffic stays valid while these are unchanged.
+KERNEL_SOURCES = ("voge_api.cu", "voge_backward.cu", "voge_device.cuh", "voge_forward.cu", "voge_project.cu",
+                  "voge_trace.cu", "voge_trace.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_15401_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -545,6 +552,27 @@ def main():
                                                                                   1e-30)}
                for k, (n, t) in trace.items()}
 
+    # ------------------------------------------------ measured ALU ceilings
+    # Register-only loops of the FMA, ex2 and both pair terms on this GPU: the
+    # measured counterpart of the derived peak, and the speed-of-light of the
+    # pair loops (algorithmic pairs per second of each tile kernel against it).
+    alu = None if args.no_alu_ceilings else voge.voge_measure_alu_peaks()
+    torch.cuda.synchronize()
+    pair_frac = {}
+    for side, prefix, key in (("fwd", "k_render", "fwd_gpairs"), ("bwd", "k_backward", "bwd_gpairs")):
+        ent = [(k, n, t) for k, (n, t) in trace.items() if k.startswith(prefix) and n > 0]
+        if alu and ent and alu[key] > 0:
+            k, n, t = max(ent, key=lambda e: e[2])
+            got = pairs / (t / n / 1e3) / 1e9
+            pair_frac[side] = {"kernel": k, "achieved_gpairs": got, "ceiling_gpairs": alu[key], "frac": got / alu[key]}
+    alu_ceilings = None if alu is None else {
+        "fma_tflops": alu["fma_tflops"], "ex2_tops": alu["ex2_tops"], "fwd_gpairs": alu["fwd_gpairs"],
+        "bwd_gpairs": alu["bwd_gpairs"], "pairs": pair_frac,
+        "how": "voge_measure_alu_peaks: register-only loops on every SM, CUDA events"}
+    if roofline is not None and alu and alu["fma_tflops"] > 0:
+        roofline["peak_measured"] = alu["fma_tflops"]
+        roofline["frac_of_measured"] = roofline["achieved"] / alu["fma_tflops"]
+
     # ------------------------------------------------ e2e through host buffers
     e2e = None
     if not args.no_e2e:
@@ -645,7 +673,7 @@ def main():
                "config": workload_config(world),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
                "serving": serving, "sampler": sampler, "posefit": posefit, "converters": converters,
-               "clocks": clk, "kernels": kernels, "loss": float(loss.item())}
+               "clocks": clk, "kernels": kernels, "alu_ceilings": alu_ceilings, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

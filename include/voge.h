@@ -409,6 +409,33 @@ int voge_trace_enable(int on); /* returns the previous state */
 int voge_trace_read(voge_trace_entry* out, int max_entries);
 void voge_trace_reset(void);
 
+/*
+ * Measured arithmetic ceilings (an aid for measurement, not a paper step).
+ * The render path runs on the FP32 and MUFU pipes: the pair term of Eq. 7 in
+ * the forward pass and its adjoint in the backward pass.  This call measures,
+ * on every SM of the current device, the rates of register-only loops:
+ *   fma_tflops  FP32 fused multiply-add, 2 FLOP each, in TFLOP/s;
+ *   ex2_tops    ex2.approx on the MUFU pipe, in 10^12 per second;
+ *   fwd_gpairs  the forward pair term (u, erf by A&S 7.1.28 and the signed
+ *               accumulation into A_k, exactly as the forward kernel does it),
+ *               in 10^9 pairs per second, at the forward kernel's occupancy;
+ *   bwd_gpairs  the backward pair adjoint (A&S 7.1.26 with e^{-u^2} and the
+ *               four accumulations), in 10^9 pairs per second, at the backward
+ *               kernel's occupancy;
+ *   ms[4]       the timed launch of each, in milliseconds; sms the SM count.
+ * Each loop runs once untimed and once timed between CUDA events on
+ * `stream`, about 20 ms each; the call returns after the stream has finished
+ * them.  Allocates nothing.  VOGE_ERR_ARG for a NULL `out`, VOGE_ERR_CUDA on a
+ * CUDA failure.
+ */
+typedef struct {
+    double fma_tflops, ex2_tops, fwd_gpairs, bwd_gpairs;
+    double ms[4];
+    int32_t sms, pad;
+} voge_alu_peaks;
+
+int voge_measure_alu_peaks(voge_alu_peaks* out, voge_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,12 @@ class voge_trace_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class voge_alu_peaks(ctypes.Structure):
+    _fields_ = [("fma_tflops", ctypes.c_double), ("ex2_tops", ctypes.c_double), ("fwd_gpairs", ctypes.c_double),
+                ("bwd_gpairs", ctypes.c_double), ("ms", ctypes.c_double * 4), ("sms", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 class voge_params(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("tau", ctypes.c_float), ("thresh", ctypes.c_float), ("flags", ctypes.c_int32),
@@ -95,6 +101,8 @@ def lib():
             L.voge_trace_read.argtypes = [P(voge_trace_entry), ctypes.c_int]
             L.voge_trace_read.restype = ctypes.c_int
             L.voge_trace_reset.restype = None
+            L.voge_measure_alu_peaks.argtypes = [P(voge_alu_peaks), vp]
+            L.voge_measure_alu_peaks.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -278,6 +286,16 @@ def voge_trace_read():
 
 def voge_trace_reset():
     lib().voge_trace_reset()
+
+
+def voge_measure_alu_peaks(stream=None):
+    """Measured arithmetic ceilings of the current GPU (register-only loops on
+    every SM, about 0.2 s): FP32 FMA TFLOP/s, MUFU ex2 rate (10^12/s), and the
+    forward and backward pair terms of Eq. 7 in 10^9 pairs/s."""
+    out = voge_alu_peaks()
+    _check(lib().voge_measure_alu_peaks(ctypes.byref(out), _stream(stream)), "voge_measure_alu_peaks")
+    return {"fma_tflops": out.fma_tflops, "ex2_tops": out.ex2_tops, "fwd_gpairs": out.fwd_gpairs,
+            "bwd_gpairs": out.bwd_gpairs, "ms": list(out.ms), "sms": int(out.sms)}
 
 
 # -------------------------------------------------------------- helpers ---

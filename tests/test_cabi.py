@@ -91,6 +91,7 @@ def test_invalid_arguments_rejected_without_launch(voge):
     assert rc == -1
     rc = L.voge_render_bwd(cams, ctypes.byref(p), fake, fake, fake, fake, None, None, None, None, None, None, 0, None)
     assert rc == -1  # grad_image missing
+    assert L.voge_measure_alu_peaks(None, None) == -1  # no output struct
 
 
 def test_pose_to_RT_matches_oracle(voge):
