@@ -57,6 +57,23 @@ __device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd
     return src;
 }
 
+// Transpose a 32 x 32 bit matrix held one row per lane (bit c of lane r is
+// entry (r, c)): afterwards lane c holds column c.  Each butterfly stage swaps
+// the off-diagonal blocks of size j inside the blocks of size 2j (Hacker's
+// Delight, 7-3, with the row exchanges done by warp shuffles).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu : j == 2 ? 0x33333333u
+                                                                                                     : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        // the lower lane of a pair keeps its low blocks and takes the partner's
+        // low blocks into its high ones; the upper lane the reverse
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+    }
+    return x;
+}
+
 template <int KM, int TH>
 __device__ __forceinline__ void render_tile(const Args& a, int t) {
     constexpr int NT = 16 * TH;
@@ -144,36 +161,27 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             } else {
                 row_masks<TH>(r0, r1, r2, r3, Qeta, tx, ty, siv + tid, NT);
             }
-        } else if (tid < ((nc + 7) & ~7)) {
-#pragma unroll
-            for (int rr = 0; rr < TH; ++rr) siv[rr * NT + tid] = kRowEmpty;  // pad the last group of eight
         }
         __syncthreads();
-        if (active) {
-            // 1) this pixel's hits in the chunk, as a bit mask (cheap, uniform):
-            //    bit jl of each candidate's row mask, eight candidates per
-            //    16-byte read, gathered with shifts into one 32-bit word per
-            //    32 candidates
-            constexpr int NW = NT / 32;
-            const int jl = tid & 15, rr = tid >> 4;
-            const uint4* ivrow = reinterpret_cast<const uint4*>(siv + rr * NT);
+        constexpr int NW = NT / 32;
+        if (__any_sync(0xffffffffu, active)) {
+            // 1) the hit masks of the warp's 32 pixels (two tile rows), one
+            //    32-bit word per 32 candidates: lane q supplies candidate q's
+            //    coverage of the two rows (its row masks, 16 bits each) and a
+            //    bit transpose hands each lane its pixel's bits
+            const int lane = tid & 31, r2 = 2 * (tid >> 5);
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 uint32_t m = 0;
-#pragma unroll
-                for (int g8 = 0; g8 < 4; ++g8) {
-                    const int q0 = w * 32 + g8 * 8;
-                    if (q0 < nc) {
-                        const uint4 x = ivrow[q0 >> 3];
-                        // candidate 2i sits in bits 0-15 of word i, candidate 2i+1 in bits 16-31
-                        const uint32_t t = ((x.x >> jl) & 0x10001u) | (((x.y >> jl) & 0x10001u) << 2) |
-                                           (((x.z >> jl) & 0x10001u) << 4) | (((x.w >> jl) & 0x10001u) << 6);
-                        const uint32_t v = (t & 0x55u) | ((t >> 15) & 0xaau);
-                        m |= v << (g8 * 8);
-                    }
+                if (w * 32 < nc) {  // uniform
+                    const int q = w * 32 + lane;
+                    const uint32_t x = q < nc ? (uint32_t)siv[r2 * NT + q] | ((uint32_t)siv[(r2 + 1) * NT + q] << 16) : 0u;
+                    m = warp_transpose32(x, lane);
                 }
                 smask[w * NT + tid] = m;
             }
+        }
+        if (active) {
             // 2) each lane walks its own hits: lanes of a warp trace different
             //    candidates at the same time instead of the union of all hits.
             //    One cursor runs over all mask words, so the warp iterates as
