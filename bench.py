@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -102,7 +103,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples; VOGE_CLOCKS_DIR keeps them somewhere lasting
+        d = os.environ.get("VOGE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"voge_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
