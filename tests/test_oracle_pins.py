@@ -282,6 +282,21 @@ def test_closed_form_weights_against_quadrature_bound():
     assert 1e-4 < dW.mean() <= 0.01  # the approximation is not exact, and small on average
 
 
+def test_fine_on_given_lists_reproduces_render():
+    """The fine pass on given lists (what CUDA parity compares against) equals
+    the render's own fine pass on the lists it selected, bit for bit, on a
+    dense scene and on a thresholded multi-pixel one."""
+    cases = [(scenes.plain_64(seed=12), 0, 0.0), (scenes.posefit_256(seed=12, N=800, C=5), 20, 1e-3)]
+    for sc, K, eta in cases:
+        cams = scenes.cameras(sc, oracle.pose_to_RT)
+        pix = oracle.all_pixels(cams)[::5]
+        r = oracle.render(cams, sc["means"], sc["inv_cov"], sc["attr"], K=K, tau=1.0, eta=eta, pix=pix)
+        assert r["count"].sum() > 0
+        f = oracle.fine(cams, sc["means"], sc["inv_cov"], sc["attr"], 1.0, r["pix"], r["idx"])
+        np.testing.assert_array_equal(f["image"], r["image"])
+        np.testing.assert_array_equal(f["weights"], r["weights"])
+
+
 # ------------------------------------------------------- selection -------
 def test_selection_matches_brute_force_sort():
     """The kept list is exactly the K smallest (l, index) among kernels with a > eta (App. A.3)."""
