@@ -91,7 +91,46 @@ def test_invalid_arguments_rejected_without_launch(voge):
     assert rc == -1
     rc = L.voge_render_bwd(cams, ctypes.byref(p), fake, fake, fake, fake, None, None, None, None, None, None, 0, None)
     assert rc == -1  # grad_image missing
-    assert L.voge_measure_alu_peaks(None, None) == -1  # no output struct
+
+
+def test_helper_entry_points_check_arguments_before_any_cuda_call(voge):
+    """Every entry point validates its sizes and pointers on the host before it
+    touches CUDA: invalid calls return VOGE_ERR_ARG (-1) and empty ones VOGE_OK
+    (0), here on a machine without a GPU."""
+    L = voge.lib()
+    S = voge._server_lib()
+    fake = ctypes.c_void_p(256)
+    # neural sampler (Eq. 10)
+    assert L.voge_sample(-1, 3, 4, 2, None, None, None, None, None, None) == -1  # negative pixel count
+    assert L.voge_sample(10, 3, 4, 0, None, None, None, None, None, None) == -1  # no channels
+    assert L.voge_sample(10, 3, 4, 2, None, None, None, None, None, None) == -1  # missing buffers
+    assert L.voge_sample(10, 3, 0, 2, fake, fake, fake, None, None, None) == 0   # no kernels: nothing to do
+    # converters (App. A.4)
+    assert L.voge_points_to_gaussians(10, 0, 0.5, None, None, None, None) == -1  # m < 1
+    assert L.voge_points_to_gaussians(10, 10, 0.5, None, None, None, None) == -1  # m >= V
+    assert L.voge_points_to_gaussians(10, 3, 1.5, None, None, None, None) == -1  # zeta outside (0, 1)
+    assert L.voge_mesh_to_gaussians(4, 1, None, None, 0.5, -1.0, None, None, None, 0, None) == -1  # flatten < 0
+    assert L.voge_mesh_to_gaussians(4, 1, fake, None, 0.5, 0.0, fake, fake, fake, 1 << 20, None) == -1  # no faces
+    # pose gradient, loss gradient and optimiser
+    assert L.voge_pose_grad(None, None, None, -1, None) == -1
+    assert L.voge_pose_grad(None, None, None, 0, None) == 0
+    assert L.voge_mse_grad(None, None, -1, None, None, None) == -1
+    assert L.voge_mse_grad(None, None, 0, None, None, None) == 0
+    assert L.voge_adam_step(fake, fake, fake, fake, 10, 0.1, 0.9, 0.999, 1e-8, 0, None) == -1  # step < 1
+    assert L.voge_adam_step(None, None, None, None, 10, 0.1, 0.9, 0.999, 1e-8, 1, None) == -1  # missing buffers
+    # serving: configurations and handles
+    cfg = voge.voge_server_config(device=0, max_slots=4, mem_budget_bytes=1024)  # below the 1 MiB minimum
+    out = ctypes.c_void_p()
+    assert S.voge_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
+    cfg = voge.voge_server_config(device=0, max_slots=0, mem_budget_bytes=64 << 20)  # no slot
+    assert S.voge_server_create(ctypes.byref(cfg), ctypes.byref(out)) == -1
+    ticket = ctypes.c_uint64()
+    assert S.voge_server_submit(None, None, ctypes.byref(ticket)) == -1
+    assert S.voge_server_wait(None, 1, 0, None) == -1
+    assert S.voge_server_pause(None, 1) == -1
+    assert S.voge_server_remove_scene(None, 0) == -1
+    assert S.voge_server_destroy(None) == -1
+    assert L.voge_measure_alu_peaks(None, None) == -1
 
 
 def test_pose_to_RT_matches_oracle(voge):
