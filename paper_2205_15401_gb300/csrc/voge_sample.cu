@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(256) k_sample(int64_t P, int L, int N, int C, 
 }
 
 // Wide 16-byte rows: lanes holding the same kernel in a slot add one summed row.
-__global__ void __launch_bounds__(256) k_sample_grouped(int64_t P, int L, int N, int C, const int32_t* __restrict__ idx,
-                                                const float* __restrict__ W, const float* __restrict__ phi,
-                                                float* num, float* wsum) {
-    // per warp: the slot's weights, kernels and same-kernel lane masks
+__global__ void __launch_bounds__(256) k_sample_grouped(int64_t P, int L, int N, int C,
+                                                        const int32_t* __restrict__ idx, const float* __restrict__ W,
+                                                        const float* __restrict__ phi, float* num, float* wsum) {
+    // per warp of the 256-thread block: the slot's weights, kernels and same-kernel lane masks
     __shared__ float s_w[8][32];
     __shared__ int32_t s_g[8][32];
     __shared__ unsigned s_grp[8][32];
