@@ -417,6 +417,23 @@ KERNEL_SOURCES = ("voge_api.cu", "voge_backward.cu", "voge_device.cuh", "voge_fo
                   "voge_trace.cu", "voge_trace.cuh")
 
 
+# The kernels of the forward pass (projection, binning, tile sort, render) and
+# of the backward pass (adjoint, gradient finalisation, pose chain) by name.
+FWD_KERNELS = ("k_project", "k_tile_totals", "k_scan_tiles", "k_scatter", "k_sort_tiles", "k_render")
+BWD_KERNELS = ("k_backward", "k_grad_finalize", "k_pose_grad")
+
+
+def pass_throughput(trace, pixels_per_step, steps):
+    """Mpix/s of the forward and of the backward pass alone, from the traced
+    device time of their kernels per step (the step also runs MSE and Adam)."""
+    out = {}
+    for name, prefixes in (("fwd", FWD_KERNELS), ("bwd", BWD_KERNELS)):
+        ms = sum(t for k, (n, t) in trace.items() if k.startswith(prefixes)) / max(steps, 1)
+        if ms > 0:
+            out[name] = {"mpix_s": pixels_per_step / (ms / 1e3) / 1e6, "ms_per_step": ms}
+    return out or None
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_15401_gb300", "csrc")
@@ -528,6 +545,7 @@ def main():
     ms_max, pix_all = reduce_over_ranks(ms, P * args.steps, world, dev)
     value = pix_all / (ms_max / 1e3) / 1e6
     launches = sum(n for n, _ in trace.values())
+    passes = pass_throughput(trace, P, args.steps)
 
     # ------------------------------------------------ roofline of the top kernel
     cnt = (index[:, : r.L] >= 0).sum(1).to(torch.float64)
@@ -676,7 +694,7 @@ def main():
                "config": workload_config(world),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
                "serving": serving, "sampler": sampler, "posefit": posefit, "converters": converters,
-               "clocks": clk, "kernels": kernels, "alu_ceilings": alu_ceilings, "loss": float(loss.item())}
+               "clocks": clk, "kernels": kernels, "passes": passes, "alu_ceilings": alu_ceilings, "loss": float(loss.item())}
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

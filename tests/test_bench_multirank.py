@@ -46,3 +46,17 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         steps, warmup, gpus, seed = 1, 0, 2, 0
 
     assert bench.run_reference(A()) is None  # returns at once, prints nothing
+
+
+def test_pass_throughput_from_traced_kernels():
+    """Forward and backward Mpix/s come from the traced time of their kernels only."""
+    import bench
+
+    trace = {"k_project": (2, 0.1), "k_tile_totals": (2, 0.02), "k_scan_tiles": (2, 0.02), "k_scatter": (2, 0.06),
+             "k_sort_tiles": (2, 0.1), "k_render<20>": (2, 1.5), "k_backward<20>": (2, 1.4),
+             "k_grad_finalize": (2, 0.08), "k_pose_grad_shared": (2, 0.02), "k_mse": (2, 0.04), "k_adam": (2, 0.02)}
+    out = bench.pass_throughput(trace, 1_000_000, 2)
+    assert abs(out["fwd"]["ms_per_step"] - 0.9) < 1e-12
+    assert abs(out["bwd"]["ms_per_step"] - 0.75) < 1e-12
+    assert abs(out["fwd"]["mpix_s"] - 1e6 / 0.9e-3 / 1e6) < 1e-6
+    assert bench.pass_throughput({}, 10, 1) is None
