@@ -1,6 +1,6 @@
 """Measured arithmetic ceilings (the roofline denominators of the pair loops):
-each rate is positive, below what the SM count and the maximum clock allow,
-and the pair terms cost more than one FMA each."""
+each rate is positive and below what the SM count and the maximum clock
+allow, and each pair term costs more than ten FP32 instructions."""
 import pytest
 import torch
 
@@ -23,5 +23,4 @@ def test_alu_ceilings_are_physical():
     lanes_per_s = sms * 128 * clock_ghz * 1e9
     for key in ("fwd_gpairs", "bwd_gpairs"):
         assert 0.0 < pk[key] * 1e9 < lanes_per_s / 10, (key, pk[key])
-    assert pk["bwd_gpairs"] < pk["fwd_gpairs"]  # the adjoint does more per pair
     assert all(t > 1.0 for t in pk["ms"])  # long enough to time with events
