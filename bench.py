@@ -163,6 +163,31 @@ def oracle_sample(sc, cams, n_pix, rng, nthreads):
     return time.perf_counter() - t0
 
 
+def oracle_configs(nthreads, seed=0):
+    """The oracle's forward + backward on the two smaller workloads: the whole
+    64x64 dense frame (128 Gaussians, every candidate kept, no threshold) and
+    8192 random pixels of the 256x256 feature scene (4000 Gaussians, C = 128)."""
+    import oracle
+    from paper_2205_15401_gb300 import scenes
+
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, sc, n_pix in (("plain_64", scenes.plain_64(seed=0), None),
+                            ("posefit_256", scenes.posefit_256(seed=0), 8192)):
+        cams = scenes.cameras(sc, oracle.pose_to_RT)
+        pix = oracle.all_pixels(cams)
+        if n_pix is not None:
+            pix = np.ascontiguousarray(pix[np.sort(rng.choice(pix.shape[0], n_pix, replace=False))])
+        m, p, a = (sc[k].astype(np.float64) for k in ("means", "inv_cov", "attr"))
+        t0 = time.perf_counter()
+        fwd = oracle.render(cams, m, p, a, K=sc["K"], tau=sc["tau"], eta=sc["eta"], pix=pix, nthreads=nthreads)
+        g = rng.standard_normal(fwd["image"].shape)
+        oracle.render_bwd(cams, m, p, a, sc["tau"], pix, fwd["idx"], g, nthreads=nthreads)
+        t = time.perf_counter() - t0
+        out[name] = {"value": pix.shape[0] / t / 1e6, "unit": UNIT, "pixels": int(pix.shape[0]), "seconds": t}
+    return out
+
+
 def cpu_baseline(sc, cams, target_s, seed=0):
     nthreads = os.cpu_count() or 1
     rng = np.random.default_rng(seed)
@@ -172,7 +197,8 @@ def cpu_baseline(sc, cams, target_s, seed=0):
     t = oracle_sample(sc, cams, n, rng, nthreads)
     return {"value": n / t / 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{n} random pixels of the 8x512x512 views, FP64 forward (all {WORKLOAD['N']} Gaussians "
-                      f"tested per pixel) + analytic backward, {t:.1f} s"}
+                      f"tested per pixel) + analytic backward, {t:.1f} s",
+            "other_workloads": oracle_configs(nthreads, seed)}
 
 
 def run_reference(args):

@@ -60,3 +60,13 @@ def test_pass_throughput_from_traced_kernels():
     assert abs(out["bwd"]["ms_per_step"] - 0.75) < 1e-12
     assert abs(out["fwd"]["mpix_s"] - 1e6 / 0.9e-3 / 1e6) < 1e-6
     assert bench.pass_throughput({}, 10, 1) is None
+
+
+def test_oracle_timings_of_the_smaller_workloads():
+    """The CPU baseline also times the oracle on the whole 64x64 dense frame
+    and on a pixel sample of the 256x256 feature scene."""
+    import bench
+
+    out = bench.oracle_configs(2)
+    assert out["plain_64"]["pixels"] == 64 * 64 and out["posefit_256"]["pixels"] == 8192
+    assert all(v["value"] > 0 and v["seconds"] > 0 for v in out.values())
