@@ -73,6 +73,8 @@ def _load():
             lib.vo_render_bwd.argtypes = [P(Camera), P(Params), P(d), P(d), P(d), P(i32), i64, P(i32), ctypes.c_int,
                                           P(d), ctypes.c_int, P(d), P(d), P(d), P(d)]
             lib.vo_quad_weights.argtypes = [P(d), P(d), P(d), ctypes.c_int, d, P(d)]
+            lib.vo_quad_weight.argtypes = [P(d), P(d), P(d), ctypes.c_int, d, ctypes.c_int]
+            lib.vo_quad_weight.restype = d
             _lib = lib
     return _lib
 
@@ -246,10 +248,14 @@ def bbox(cams, means, inv_cov, eta):
     return out
 
 
-def quad_weights(l, a, b, tau):
-    """Exact W_k = int T(t) rho_k(t) dt along one ray for kernels (l, a, b)."""
+def quad_weights(l, a, b, tau, k=None):
+    """Exact W_k = int T(t) rho_k(t) dt along one ray for kernels (l, a, b):
+    every kernel's, or kernel k's alone (a float) when k is given."""
     lib = _load()
     l, a, b = _f64(l).reshape(-1), _f64(a).reshape(-1), _f64(b).reshape(-1)
+    if k is not None:
+        return float(lib.vo_quad_weight(_ptr(l, ctypes.c_double), _ptr(a, ctypes.c_double),
+                                        _ptr(b, ctypes.c_double), int(l.shape[0]), float(tau), int(k)))
     out = np.zeros(l.shape[0])
     lib.vo_quad_weights(_ptr(l, ctypes.c_double), _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double),
                         int(l.shape[0]), float(tau), _ptr(out, ctypes.c_double))

@@ -618,20 +618,23 @@ static double simpson_rec(const qctx_t* q, double lo, double hi, double flo, dou
            simpson_rec(q, mid, hi, fmid, frm, fhi, right, 0.5 * eps, depth - 1);
 }
 
+/* W_exact of kernel k among the n kernels (l, a, b) of one ray. */
+double vo_quad_weight(const double* l, const double* a, const double* b, int n, double tau, int k) {
+    qctx_t q = {l, a, b, n, k, tau};
+    /* integrate x in [-14, 14] as 28 unit panels, each adaptively */
+    double acc = 0.0;
+    for (int s = -14; s < 14; s++) {
+        double lo = s, hi = s + 1.0;
+        double flo = q_integrand(&q, lo), fhi = q_integrand(&q, hi), fmid = q_integrand(&q, 0.5 * (lo + hi));
+        double whole = (hi - lo) / 6.0 * (flo + 4.0 * fmid + fhi);
+        acc += simpson_rec(&q, lo, hi, flo, fmid, fhi, whole, 1e-14, 40);
+    }
+    return acc;
+}
+
 /* W_exact[k] for the n kernels (l, a, b) of one ray. */
 void vo_quad_weights(const double* l, const double* a, const double* b, int n, double tau, double* W_exact) {
-    for (int k = 0; k < n; k++) {
-        qctx_t q = {l, a, b, n, k, tau};
-        /* integrate x in [-14, 14] as 28 unit panels, each adaptively */
-        double acc = 0.0;
-        for (int s = -14; s < 14; s++) {
-            double lo = s, hi = s + 1.0;
-            double flo = q_integrand(&q, lo), fhi = q_integrand(&q, hi), fmid = q_integrand(&q, 0.5 * (lo + hi));
-            double whole = (hi - lo) / 6.0 * (flo + 4.0 * fmid + fhi);
-            acc += simpson_rec(&q, lo, hi, flo, fmid, fhi, whole, 1e-14, 40);
-        }
-        W_exact[k] = acc;
-    }
+    for (int k = 0; k < n; k++) W_exact[k] = vo_quad_weight(l, a, b, n, tau, k);
 }
 
 /* Neural sampler, Sec. 3.4 Eq. 10, on given per-pixel lists and weights:

@@ -244,6 +244,54 @@ def test_quadrature_far_apart_kernels():
     assert W[1] == pytest.approx(math.exp(-tau * a1) * (1 - math.exp(-tau * a2)) / tau, rel=1e-9)
 
 
+def _narrow_pair_scene(lj, aj, bj, lk, ak, bk, sx=0.3):
+    """A 1x1 view whose ray is D = (0, 0, 1) and two kernels on it: kernel 0 of
+    peak density aj, depth lj and b = DᵀPD = bj; kernel 1 likewise.  Each is an
+    axis-aligned ellipsoid offset along x so that qt = x^2 / sx^2 gives the
+    wanted a = e^{-qt/2}; its z extent sets b, and l is its z."""
+    cam = {"R": np.eye(3), "T": np.zeros(3), "F": 1.0, "Ox": 0.5, "Oy": 0.5, "H": 1, "W": 1}
+    M = np.array([[sx * math.sqrt(2 * math.log(1 / aj)), 0.0, lj], [sx * math.sqrt(2 * math.log(1 / ak)), 0.0, lk]])
+    v = 1.0 / sx**2
+    P = np.array([[v, 0, 0, v, 0, bj], [v, 0, 0, v, 0, bk]])
+    return cam, M, P
+
+
+@pytest.mark.parametrize("aj,bj,ak,tau", [(0.8, 4.0, 0.6, 1.0), (0.5, 9.0, 0.9, 2.0), (0.95, 1.0, 0.3, 0.5)])
+def test_erf_argument_scale_from_narrow_kernel_limit(aj, bj, ak, tau):
+    """Pins the erf argument of Eq. 7, (l_k - l_j) / (sqrt2 sigma_j) with
+    1/sigma_j^2 = DᵀP_jD, at intermediate values (the other pins see only
+    erf(0) and erf(+-inf)).
+
+    When kernel k is very narrow along the ray (b_k -> inf), T from the other
+    kernels is constant across it, so the outer integral of Eq. 1 has the
+    closed form W_exact_k = exp(-tau A_-k(l_k)) (1 - e^{-tau a_k}) / tau, with
+    A_-k the exact inner integral of kernel j at l_k.  Eq. 7 gives
+    W'_k = exp(-tau (A_-k(l_k) + a_k/2)) a_k, the same A_-k through erf.  Hence
+    W'_k (1 - e^{-tau a_k}) / (tau a_k e^{-tau a_k/2}) must equal the limit of
+    the quadrature of Eq. 1 (itself pinned by the single-kernel closed form)
+    for every separation, in front of kernel j and behind it.  The quadrature's
+    distance from its limit falls as 1/sqrt(b_k), so the limit is taken by
+    Richardson extrapolation from b_k = 1e8 and 1e10 (left over: below 1e-9).
+    A misread scale (erf((l_k - l_j) sqrt(b_j)), or r_k in place of r_j)
+    misses by 1e-2 or more."""
+    lj = 3.0
+    for u in (-2.0, -1.0, -0.4, -0.2, 0.2, 0.4, 0.7, 1.0, 1.5, 2.0):
+        lk = lj + u / math.sqrt(bj / 2)  # u_kj = (l_k - l_j) sqrt(b_j / 2)
+        W_exact = {}
+        for bk in (1e8, 1e10):
+            cam, M, P = _narrow_pair_scene(lj, aj, bj, lk, ak, bk)
+            tr = [oracle.trace_dir(M[g], P[g], [0.0, 0.0, 1.0]) for g in (0, 1)]
+            W_exact[bk] = oracle.quad_weights([t[0] for t in tr], [math.exp(-0.5 * t[1]) for t in tr],
+                                              [t[2] for t in tr], tau, k=1)
+        W_inf = (10.0 * W_exact[1e10] - W_exact[1e8]) / 9.0
+        r = oracle.render([cam], M, P, np.ones((2, 1)), K=0, tau=tau, eta=0.0)
+        pos = list(r["idx"][0]).index(1)
+        a_k = r["a"][0][pos]
+        assert a_k == pytest.approx(ak, rel=1e-12)
+        W_limit = r["weights"][0][pos] * (1 - math.exp(-tau * a_k)) / (tau * a_k * math.exp(-tau * a_k / 2))
+        assert abs(W_limit - W_inf) <= 1e-8, (u, W_limit, W_inf)
+
+
 def _approximation_errors(sc, pix):
     """W_exact - W' per kept entry along each ray of ``pix``: W' is Eq. 7's
     closed form (the oracle's render), W_exact the outer integral of Eq. 1 by
