@@ -355,10 +355,9 @@ int voge_server_destroy(voge_server* s);
 /*
  * Forward render that allocates nothing and takes no workspace.  The paper
  * has no counterpart: this entry point exists for callers that cannot
- * allocate device memory where they render (code inside a region that
- * forbids cudaMalloc, such as a host callback or a real-time loop with a
- * memory budget fixed up front, or a program that links only this library
- * and has no allocator of its own).
+ * allocate device memory where they render -- a real-time loop whose device
+ * memory budget is fixed up front and must not grow, or a program that links
+ * only this library and has no allocator of its own.
  *
  * It behaves as voge_render_fwd (same arguments and outputs, minus the
  * workspace) but uses a workspace of VOGE_STATIC_WORKSPACE_BYTES that lives
@@ -366,9 +365,8 @@ int voge_server_destroy(voge_server* s);
  * until the process exits.
  *   - Returns VOGE_ERR_WORKSPACE, and launches nothing, if
  *     voge_workspace_bytes(cams, p) exceeds VOGE_STATIC_WORKSPACE_BYTES.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *   - Each call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing) and passes it on.
  *   - Every call on a device shares the one array, which keeps the previous
  *     call's contents (each call clears what must start at zero).  Calls whose
  *     work overlaps on the GPU -- for example on two streams -- race on it:

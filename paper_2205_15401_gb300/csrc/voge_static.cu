@@ -1,38 +1,28 @@
 // voge_static.cu -- forward render without a caller-provided workspace.
 //
 // Some callers cannot allocate device memory at the point where they render:
-// code running inside a region that forbids cudaMalloc (for example a host
-// callback or a real-time loop whose memory budget is fixed up front), or a
-// host program that links only this library and owns no allocator.  For them
-// voge_render_fwd_static() uses a workspace that lives in the library itself:
-// a file-scope device array of VOGE_STATIC_WORKSPACE_BYTES that every GPU
-// loading the library holds until the process exits.  Nothing here calls
-// cudaMalloc, cudaFree or any allocating routine.
-#include <mutex>
-
+// a real-time loop whose device memory budget is fixed up front and must not
+// grow, or a host program that links only this library and owns no
+// allocator.  For them voge_render_fwd_static() uses a workspace that lives
+// in the library itself: a file-scope device array of
+// VOGE_STATIC_WORKSPACE_BYTES that every GPU loading the library holds until
+// the process exits.  Nothing here calls cudaMalloc, cudaFree or any
+// allocating routine.
 #include "../../include/voge.h"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_static_workspace[VOGE_STATIC_WORKSPACE_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the array on the current device, looked up once per
-// device (the host-side symbol is only a stand-in and must never be passed
-// to a kernel).
+// Device address of the array in the current device's context.  The
+// host-side symbol is only a stand-in and must never reach a kernel.  The
+// address is looked up on every call (the lookup allocates nothing): a
+// context that was torn down and created again (cudaDeviceReset) loads the
+// module anew, and the array may then sit at another address.
 int static_workspace(void** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VOGE_ERR_CUDA;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_workspace) != cudaSuccess || !p) return VOGE_ERR_CUDA;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_workspace) != cudaSuccess || !p) return VOGE_ERR_CUDA;
+    *out = p;
     return VOGE_OK;
 }
 

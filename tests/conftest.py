@@ -25,3 +25,21 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Lists that differ from the oracle's at allowed FP32/FP64 ties, per
+    forward check, and each gradient check's margins."""
+    try:
+        from parity import GRAD_STATS, LIST_DIFFS
+    except Exception:  # pragma: no cover
+        return
+    tr = terminalreporter
+    if LIST_DIFFS:
+        tr.section("index lists differing at allowed ties")
+        for name, n_diff, total in LIST_DIFFS:
+            tr.write_line(f"{n_diff:6d} of {total:8d}  {name}")
+    if GRAD_STATS:
+        tr.section("gradient parity: relative norm error (bound 1e-3), worst per-element error / its bound")
+        for name, key, rel, exc in GRAD_STATS:
+            tr.write_line(f"{rel:9.2e} {exc:9.3f}  {key:10s} {name}")

@@ -1,6 +1,6 @@
 """Parity checks of the CUDA path against the FP64 oracle.
 
-Tolerances (stated here and in the design doc):
+Tolerances:
   image, weights     1e-4 absolute against the oracle's Eq. 7-8 evaluated in
                      FP64 on the GPU's own lists
   index lists        identical, except where the FP32 decision may differ from
@@ -9,8 +9,12 @@ Tolerances (stated here and in the design doc):
                      1e-5 eta (at the threshold: the FP32 qt carries a relative
                      error of a few ulp times qt <= 2 ln(1/eta) <= 18.5, i.e.
                      below 5e-6 in a), or either of those at the K-th place
-  gradients          ||g - g_ref|| / ||g_ref|| <= 1e-3 per tensor
+  gradients          ||g - g_ref|| / ||g_ref|| <= 1e-3 per tensor, and per
+                     element |g - g_ref| <= 1e-3 (|g_ref| + 1e-3 max|g_ref|)
+                     (lists frozen: no gradient flows through the selection)
 """
+import os
+
 import numpy as np
 
 import oracle
@@ -63,11 +67,19 @@ def check_lists(gpu_idx, ref, cams, means, inv_cov, attr, K, tau, eta):
     return int(diff.size)
 
 
+# (test, lists differing at allowed ties, lists compared) of every forward check
+# and (test, tensor, relative error, per-element excess) of every gradient
+# check in the session; conftest prints them at the end of the run
+LIST_DIFFS = []
+GRAD_STATS = []
+
+
 def check_forward(image, weights, index, cams, means, inv_cov, attr, K, tau, eta, pix=None, ref=None):
     """Full forward parity on the pixels `pix` (all if None).  image/weights/index: numpy rows for those pixels."""
     if ref is None:
         ref = oracle.render(cams, means, inv_cov, attr, K=K, tau=tau, eta=eta, pix=pix, culled=eta > 0)
     n_diff = check_lists(index, ref, cams, means, inv_cov, attr, K, tau, eta)
+    LIST_DIFFS.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], n_diff, int(ref["idx"].shape[0])))
     fine = oracle.fine(cams, means, inv_cov, attr, tau, ref["pix"], index)
     err_img = np.abs(image - fine["image"]).max() if image.size else 0.0
     assert err_img <= TOL_IMAGE, f"image error {err_img}"
@@ -81,3 +93,28 @@ def rel_err(got, want):
     got = np.asarray(got, np.float64)
     want = np.asarray(want, np.float64)
     return float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30))
+
+
+def elem_excess(got, want, tol=TOL_GRAD):
+    """Largest |g - g_ref| / (tol (|g_ref| + tol max|g_ref|)) over the elements:
+    at most 1 when every element is inside the per-element bound."""
+    got = np.asarray(got, np.float64).reshape(-1)
+    want = np.asarray(want, np.float64).reshape(-1)
+    if want.size == 0:
+        return 0.0
+    bound = tol * (np.abs(want) + tol * np.abs(want).max())
+    return float((np.abs(got - want) / np.maximum(bound, 1e-300)).max())
+
+
+def check_grads(got, want, keys=("g_means", "g_inv_cov", "g_attr", "g_R", "g_T"), tol=TOL_GRAD):
+    """Gradient parity of each tensor: the norm bound and the per-element bound.
+    Returns {key: (relative norm error, per-element excess)}."""
+    out = {}
+    for k in keys:
+        assert np.linalg.norm(want[k]) > 0, f"{k}: reference gradient is zero"
+        rel, exc = rel_err(got[k], want[k]), elem_excess(got[k], want[k], tol)
+        out[k] = (rel, exc)
+        GRAD_STATS.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], k, rel, exc))
+        assert rel <= tol, f"{k}: relative error {rel}"
+        assert exc <= 1.0, f"{k}: an element exceeds its bound by {exc:.3g}x"
+    return out
