@@ -85,7 +85,13 @@ enum {
     /* voge_render_bwd only: reuse the projection that the matching
      * voge_render_fwd call left in the same workspace (same cams, params and
      * Gaussians, workspace untouched in between) instead of recomputing it. */
-    VOGE_FLAG_REUSE_PROJECTION = 2
+    VOGE_FLAG_REUSE_PROJECTION = 2,
+    /* voge_render_fwd only: run the coarse pass (selection) and the fine pass
+     * as two kernels -- the selection writes the index lists, then the fine
+     * pass of voge_render_fine reads them -- instead of one fused kernel.
+     * Same outputs up to the rounding of W (identical arithmetic); lists
+     * longer than 32 always take the fused path. */
+    VOGE_FLAG_SPLIT_FORWARD = 4
 };
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -124,6 +130,33 @@ size_t voge_workspace_bytes(const voge_camera* cams, const voge_params* p);
 int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
                     const float* attr, float* image, float* weights, int32_t* index, void* workspace,
                     size_t workspace_bytes, voge_stream_t stream);
+
+/*
+ * Fine pass alone (Eq. 7 and 8) over given per-pixel lists: for each pixel
+ * with list S_p (the entries before the first slot outside [0, N)),
+ *   A_k = sum_{j in S_p} (a_j/2)(1 + erf((l_k - l_j) sqrt(b_j/2))),
+ *   W_k = exp(-tau A_k) e^{q_k},  image_p = sum_k W_k c_k,
+ * with l, e^{q} = a and b = DᵀPD of each listed kernel on the pixel's ray
+ * (Eq. 6).  The sum is over the list in any order; it includes k itself.
+ * The selection (thresh, K) is not applied: the lists are taken as given.
+ * This is the second half of voge_render_fwd, for re-rendering from saved
+ * lists (new attributes or tau, same selection) and for checking the fine
+ * pass on its own.
+ *
+ *   cams, p    as voge_render_fwd; L = voge_list_length(p) must be <= 32
+ *              (VOGE_ERR_UNSUPPORTED otherwise)
+ *   index      device, [pixels][L] int32: each pixel's list, ended by the
+ *              first entry < 0 or >= N (typically voge_render_fwd's output)
+ *   image      device, [pixels][C] float, written
+ *   weights    device, [pixels][L] float, written: W_k in list order, 0 after
+ *              the list's end; may be NULL
+ *   workspace  device, >= voge_workspace_bytes(cams, p), 256-byte aligned
+ * Asynchronous on `stream`; allocates nothing.  VOGE_ERR_ARG / _WORKSPACE as
+ * voge_render_fwd.
+ */
+int voge_render_fine(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                     const float* attr, const int32_t* index, float* image, float* weights, void* workspace,
+                     size_t workspace_bytes, voge_stream_t stream);
 
 /*
  * Backward pass of voge_render_fwd with the kept lists frozen (the selection

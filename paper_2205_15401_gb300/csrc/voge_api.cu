@@ -12,17 +12,20 @@
 
 namespace voge {
 cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
-cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
+cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a, int fine);
+cudaError_t launch_fine(int KM, int total_tiles, int tile_h, int L, const void* index, cudaStream_t s,
+                        const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
-int render_blocks_per_sm(int KM);
+int render_blocks_per_sm(int KM, int fine);
 int backward_blocks_per_sm(int KM);
 
 // Persistent tile launches: as many CTAs as can be resident at once (cached
-// per device and variant), never more than there are tiles.
+// per device and variant), never more than there are tiles.  fwd: 0 the
+// backward, 1 the fused forward, 2 the selection-only forward.
 int tile_grid(int KM, int fwd, int total_tiles) {
     static std::mutex mu;
-    static int cache[64][2][6];
+    static int cache[64][3][6];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
@@ -30,14 +33,14 @@ int tile_grid(int KM, int fwd, int total_tiles) {
     int g;
     {
         std::lock_guard<std::mutex> lk(mu);
-        g = cache[dev][fwd ? 1 : 0][vi];
+        g = cache[dev][fwd][vi];
     }
     if (g == 0) {
         int nsm = 0;
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
-        g = nsm * (fwd ? render_blocks_per_sm(KM) : backward_blocks_per_sm(KM));
+        g = nsm * (fwd ? render_blocks_per_sm(KM, fwd == 1) : backward_blocks_per_sm(KM));
         std::lock_guard<std::mutex> lk(mu);
-        cache[dev][fwd ? 1 : 0][vi] = g;
+        cache[dev][fwd][vi] = g;
     }
     return total_tiles < g ? total_tiles : g;
 }
@@ -59,7 +62,7 @@ void pick_variant(int L, int* KM, int* TH) {
     if (L <= 8) { *KM = 8; *TH = 16; }
     else if (L <= 16) { *KM = 16; *TH = 16; }
     else if (L <= 20) { *KM = 20; *TH = 16; }
-    else if (L <= 24) { *KM = 24; *TH = 16; }
+    else if (L <= 24) { *KM = 24; *TH = 8; }
     else if (L <= kMaxRegisterList) { *KM = 32; *TH = 8; }
     else { *KM = 0; *TH = 16; }  // generic path
 }
@@ -391,11 +394,47 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
     b.image = image;
     b.weights = weights;
     b.index = index;
+    const bool split = (p->flags & VOGE_FLAG_SPLIT_FORWARD) && l.KM != 0;
+    if (split) b.index_in = index;  // the fine kernel reads the lists the selection kernel wrote
     int rc = upload_and_project(cams, p, l, a, b, 1, 1, s);
     if (rc != VOGE_OK) return rc;
     if (l.total_tiles == 0) return VOGE_OK;
-    return launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a) == cudaSuccess ? VOGE_OK
-                                                                                              : VOGE_ERR_CUDA;
+    if (!split)
+        return launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a, 1) == cudaSuccess ? VOGE_OK
+                                                                                                     : VOGE_ERR_CUDA;
+    if (launch_render_tiles(l.KM, tile_grid(l.KM, 2, l.total_tiles), s, a, 0) != cudaSuccess) return VOGE_ERR_CUDA;
+    return launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+}
+
+int voge_render_fine(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
+                     const float* attr, const int32_t* index, float* image, float* weights, void* workspace,
+                     size_t workspace_bytes, voge_stream_t stream_) {
+    if (!valid_params(cams, p) || !image) return VOGE_ERR_ARG;
+    if (p->N > 0 && (!means || !inv_cov || !attr || !index)) return VOGE_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    const Layout l = make_layout(cams, p);
+    if (!workspace || workspace_bytes < l.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return VOGE_ERR_WORKSPACE;
+    if (p->N == 0) {
+        if (weights && l.L > 0 &&
+            cudaMemsetAsync(weights, 0, sizeof(float) * (size_t)l.pixels * l.L, s) != cudaSuccess)
+            return VOGE_ERR_CUDA;
+        return cudaMemsetAsync(image, 0, sizeof(float) * (size_t)l.pixels * p->C, s) == cudaSuccess ? VOGE_OK
+                                                                                                    : VOGE_ERR_CUDA;
+    }
+    if (l.KM == 0) return VOGE_ERR_UNSUPPORTED;  // lists longer than 32
+    const Args a = make_args(l, workspace);
+    Buffers b;
+    memset(&b, 0, sizeof(b));
+    b.means = means;
+    b.inv_cov = inv_cov;
+    b.attr = attr;
+    b.image = image;
+    b.weights = weights;
+    b.index_in = index;
+    int rc = upload_and_project(cams, p, l, a, b, 1, 0, s);
+    if (rc != VOGE_OK) return rc;
+    return launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
 }
 
 int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,

@@ -95,7 +95,8 @@ struct BatchHdr {
     int32_t nviews;
     int32_t class_begin[kMaxClasses];  // tile ranges of the list-capacity classes
     int32_t class_end[kMaxClasses];
-    int32_t counters[3 * kMaxClasses]; // persistent-launch work counters (forward, backward, wide backward)
+    int32_t counters[4 * kMaxClasses]; // persistent-launch work counters (forward, backward, wide backward,
+                                       // standalone fine pass)
     int32_t shared_scene;   // 1: every view renders the same Gaussians (records rec_base = v * N)
     int32_t pad[1];
 };

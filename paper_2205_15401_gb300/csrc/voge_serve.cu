@@ -31,7 +31,7 @@
 
 namespace voge {
 cudaError_t launch_project(int grid, int tiles, int count_tiles, cudaStream_t s, const Args& a);
-cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a);
+cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a, int fine);
 cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int tile_grid(int KM, int fwd, int total_tiles);
@@ -148,7 +148,7 @@ int class_of(int L) {
     return 5;
 }
 const int kClassKM[6] = {8, 16, 20, 24, 32, 0};
-const int kClassTH[6] = {16, 16, 16, 16, 8, 16};
+const int kClassTH[6] = {16, 16, 16, 8, 8, 16};
 constexpr int kClasses = 6;
 
 struct Scene {
@@ -365,7 +365,7 @@ cudaError_t issue_tick(voge_server* S, TickSlot& ts, uint32_t mask) {
         if (!(mask & (1u << c))) continue;
         Args ac = a;
         ac.cls = c;
-        e = launch_render_tiles(kClassKM[c], tile_grid(kClassKM[c], 1, 1 << 30), s, ac);
+        e = launch_render_tiles(kClassKM[c], tile_grid(kClassKM[c], 1, 1 << 30), s, ac, 1);
         if (e != cudaSuccess) return e;
     }
     k_mse_batch<<<S->grid_records, 256, 0, s>>>(a);

@@ -28,6 +28,7 @@ _lib = None
 VOGE_OK = 0
 VOGE_FLAG_PLAIN = 1
 VOGE_FLAG_REUSE_PROJECTION = 2
+VOGE_FLAG_SPLIT_FORWARD = 4
 
 
 class voge_camera(ctypes.Structure):
@@ -69,6 +70,9 @@ def lib():
             L.voge_workspace_bytes.restype = ctypes.c_size_t
             L.voge_render_fwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
             L.voge_render_fwd.restype = ctypes.c_int
+            L.voge_render_fine.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                           vp]
+            L.voge_render_fine.restype = ctypes.c_int
             L.voge_render_bwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                           ctypes.c_size_t, vp]
             L.voge_render_bwd.restype = ctypes.c_int
@@ -172,6 +176,15 @@ def voge_render_fwd(cams, params, means, inv_cov, attr, image, weights, index, w
                                _ptr(image, f32), _ptr(weights, f32), _ptr(index, i32), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "voge_render_fwd")
+
+
+def voge_render_fine(cams, params, means, inv_cov, attr, index, image, weights, workspace, stream=None):
+    """Fine pass (Eq. 7-8) over given per-pixel lists ``index`` [P][L]."""
+    f32, i32 = torch.float32, torch.int32
+    rc = lib().voge_render_fine(cams, ctypes.byref(params), _ptr(means, f32), _ptr(inv_cov, f32), _ptr(attr, f32),
+                                _ptr(index, i32), _ptr(image, f32), _ptr(weights, f32), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "voge_render_fine")
 
 
 def voge_render_bwd(cams, params, means, inv_cov, attr, index, grad_image, grad_means, grad_inv_cov, grad_attr,
@@ -343,6 +356,13 @@ class Renderer:
                                                                flags, self.params.bin_capacity)
         voge_render_fwd(self.cams, params, means, inv_cov, attr, image, weights, index, self.workspace)
         return image, weights, index
+
+    def fine(self, means, inv_cov, attr, index, image=None, weights=None):
+        """Fine pass alone over given lists index [P][L] (voge_render_fine)."""
+        if image is None:
+            image = torch.empty((self.pixels, self.params.C), dtype=torch.float32, device=self.device)
+        voge_render_fine(self.cams, self.params, means, inv_cov, attr, index, image, weights, self.workspace)
+        return image, weights
 
     def backward(self, means, inv_cov, attr, index, grad_image, grad_means=None, grad_inv_cov=None, grad_attr=None,
                  grad_cam=None, reuse_projection=False, weights=None):

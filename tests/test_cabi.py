@@ -91,6 +91,16 @@ def test_invalid_arguments_rejected_without_launch(voge):
     assert rc == -1
     rc = L.voge_render_bwd(cams, ctypes.byref(p), fake, fake, fake, fake, None, None, None, None, None, None, 0, None)
     assert rc == -1  # grad_image missing
+    # fine pass on given lists
+    rc = L.voge_render_fine(cams, ctypes.byref(p), fake, fake, fake, fake, fake, None, None, 0, None)
+    assert rc == -2  # no workspace
+    rc = L.voge_render_fine(cams, ctypes.byref(p), fake, fake, fake, fake, None, None, fake, 1 << 30, None)
+    assert rc == -1  # no image
+    rc = L.voge_render_fine(cams, ctypes.byref(p_bad), fake, fake, fake, fake, fake, None, fake, 1 << 30, None)
+    assert rc == -1
+    p_long = voge.make_params(2, 100, 3, 40, 1.0, 0.01)
+    rc = L.voge_render_fine(cams, ctypes.byref(p_long), fake, fake, fake, fake, fake, None, fake, 1 << 30, None)
+    assert rc == -4  # lists longer than 32: VOGE_ERR_UNSUPPORTED, before any CUDA call
 
 
 def test_helper_entry_points_check_arguments_before_any_cuda_call(voge):
