@@ -16,6 +16,7 @@ cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args&
 cudaError_t launch_fine(int KM, int total_tiles, int tile_h, int L, const void* index, cudaStream_t s,
                         const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a);
+cudaError_t launch_backward_packed(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int render_blocks_per_sm(int KM, int fine);
 int backward_blocks_per_sm(int KM);
@@ -473,10 +474,13 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
     int rc = upload_and_project(cams, p, l, a, b, project, 0, s);
     if (rc != VOGE_OK) return rc;
     if (cudaMemsetAsync(a.ws.gcam, 0, 4 * kGcamStride * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
-    if (l.total_tiles > 0 &&
-        launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), weights ? 0 : 1, p->C >= 8 ? 2 : 1, s, a) !=
-            cudaSuccess)
-        return VOGE_ERR_CUDA;
+    if (l.total_tiles > 0) {
+        const bool packed = weights && p->C <= 3 && l.KM > 0 && l.KM <= 20;
+        const cudaError_t e =
+            packed ? launch_backward_packed(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a)
+                   : launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), weights ? 0 : 1, p->C >= 8 ? 2 : 1, s, a);
+        if (e != cudaSuccess) return VOGE_ERR_CUDA;
+    }
     // the finalize also folds in attribute gradients of up to three channels
     if ((grad_means || grad_inv_cov || grad_cam || grad_attr) &&
         launch_grad_finalize(record_grid(p->N), p->B, p->N, 1, s, a) != cudaSuccess)

@@ -25,9 +25,9 @@ constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
 // Camera-space gradient of one (pixel, kept Gaussian) pair: out[0..2] = dM,
 // out[3..8] = G (xx, xy, xz, yy, yz, zz) with entries of P treated as independent.
-__device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const Trace& t, const float4& r3, float px,
-                                                float py, float invF, float dqt, float dl, float db, float out[9]) {
-    const float4 s0 = __ldg(a.ws.rec2 + 2 * o), s1 = __ldg(a.ws.rec2 + 2 * o + 1);
+// s0, s1: the pair's second record (camera-space P and centre ray).
+__device__ __forceinline__ void chain_to_camera(const float4& s0, const float4& s1, const Trace& t, const float4& r3,
+                                                float invF, float dqt, float dl, float db, float out[9]) {
     const float ib = rcp_approx(t.b);
     const float Mz = r3.y;
     const float dlt = -Mz * t.num * ib;  // l - Mz
@@ -64,7 +64,10 @@ __device__ __forceinline__ void chain_to_camera(const Args& a, int64_t o, const 
 //               finalize kernel,
 //   kAttrSlot:  C <= 3 for classes without room for W_k in shared memory: the
 //               same slots, with one vector reduction of their own.
-constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3;
+//   kAttrPacked: kAttrChain with the forward's W_k supplied, the entries set
+//               up packed over the lanes (k_backward_packed, its own kernel
+//               so that its registers do not weigh on the other forms).
+constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3, kAttrPacked = 4;
 
 // Classes whose W_k buffer fits next to the stream without losing a block per SM.
 template <int KM, int TH>
@@ -129,15 +132,109 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     // With the forward's weights and narrow attributes, dA_k is formed while
     // the entries are set up (the index is in a register there).
     const float* wi = vd.weights_in ? vd.weights_in + pix * L : nullptr;
+    constexpr bool kChain = AM == kAttrChain || AM == kAttrPacked;
     const bool early = wi != nullptr && C <= 3 && AM != kAttrWarp && AM != kAttrLane;
     float ga0 = 0.0f, ga1 = 0.0f, ga2 = 0.0f;
-    if (early && valid) {
+    constexpr bool packed = AM == kAttrPacked;
+    if constexpr (packed) {
+        // Set-up with the entries packed over the lanes (the forward's W_k are
+        // supplied and C <= 3): entry i of the warp's 32 lists -- pixel p,
+        // list position k -- is set up by one lane, so that 32 entries'
+        // record, attribute, image-gradient and weight loads are in flight at
+        // once.  Its (l, r, m) go to the stream and dA_k to the W_k buffer
+        // (unused when W comes from the forward).
+        float* sdA = swk;
+        {
+            bool open = valid;
+#pragma unroll
+            for (int s = 0; s < KM; ++s) {
+                if (s < K) {
+                    const int32_t g = *stg(lane * L + s);
+                    open = open && g >= 0 && g < N;
+                    n += open ? 1 : 0;
+                }
+            }
+        }
+        __syncwarp();  // the ids are read (the stream overwrites their staging rows)
+        int incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - n;
+        auto pixel_of = [&](int i) -> int {  // the last lane p with excl_p <= i
+            int p = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int b = __shfl_sync(0xffffffffu, excl, p + step);
+                if (b <= i) p += step;
+            }
+            return p;
+        };
+        for (int i0 = 0; i0 < total; i0 += 64) {
+            int pp[2], kk[2];
+            int32_t gg[2];
+            int64_t px2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = min(i0 + 32 * h + lane, total - 1);
+                pp[h] = pixel_of(i);
+                kk[h] = i - __shfl_sync(0xffffffffu, excl, pp[h]);
+                px2[h] = (int64_t)(row0 + 2 * warp + (pp[h] >> 4)) * W + tx * kTileW + (pp[h] & 15);
+                gg[h] = __ldg(vd.index_in + px2[h] * L + kk[h]);
+            }
+            float4 r[2][4];
+            float c[2][3], gq[2][3], wk[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                load_rec(a.ws.rec, vb + gg[h], r[h][0], r[h][1], r[h][2], r[h][3]);
+                const float* ck = attr + (int64_t)gg[h] * C;
+                const float* gp0 = vd.grad_image + px2[h] * C;
+                c[h][0] = __ldg(ck);
+                gq[h][0] = __ldg(gp0);
+                c[h][1] = C > 1 ? __ldg(ck + 1) : 0.0f;
+                gq[h][1] = C > 1 ? __ldg(gp0 + 1) : 0.0f;
+                c[h][2] = C > 2 ? __ldg(ck + 2) : 0.0f;
+                gq[h][2] = C > 2 ? __ldg(gp0 + 2) : 0.0f;
+                wk[h] = __ldg(vd.weights_in + px2[h] * L + kk[h]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (i0 + 32 * h + lane < total) {
+                    const int p = pp[h];
+                    const float pxp = (float)(tx * kTileW + (p & 15)) + 0.5f;
+                    const float pyp = (float)(row0 + 2 * warp + (p >> 4)) + 0.5f;
+                    const Entry e = entry_px(r[h][0], r[h][1], r[h][2], r[h][3], pxp, pyp);
+                    const float G = fmaf(gq[h][2], c[h][2], fmaf(gq[h][1], c[h][1], gq[h][0] * c[h][0]));
+                    jst[kk[h] * NT + 32 * warp + p] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
+                    sdA[kk[h] * NT + 32 * warp + p] = -tau * G * wk[h];
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < KM; ++s) {
+            const int e = s - (KM - K);
+            dl[s] = 0.0f;
+            if (e >= 0 && e < n) {
+                const float4 J = jst[e * NT + tid];
+                hi[s] = J.x;
+                lo[s] = J.y;
+                dA[s] = sdA[e * NT + tid];
+            } else {
+                hi[s] = 0.0f;
+                lo[s] = 0.0f;
+                dA[s] = 0.0f;
+            }
+        }
+    } else if (early && valid) {
         const float* gp0 = vd.grad_image + pix * C;
         ga0 = __ldg(gp0);
         if (C > 1) ga1 = __ldg(gp0 + 1);
         if (C > 2) ga2 = __ldg(gp0 + 2);
     }
-    {
+    if constexpr (!packed) {
         int32_t id[KM];
 #pragma unroll
         for (int s = 0; s < KM; ++s) id[s] = (s >= KM - K) ? *stg(lane * L + (s - (KM - K))) : -1;
@@ -164,7 +261,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                     if (C > 2) G = fmaf(ga2, __ldg(ck + 2), G);
                     const float Wk = __ldg(wi + (s - (KM - K)));
                     dA[s] = -tau * G * Wk;
-                    if (AM == kAttrChain && !wi) swk[n * NT + tid] = Wk;
+                    if (kChain && !wi) swk[n * NT + tid] = Wk;
                     if (AM == kAttrSlot) red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * ga0, Wk * ga1, Wk * ga2);
                 }
                 ++n;
@@ -227,7 +324,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                     }
                 }
                 dA[s] = -tau * G * Wk;
-                if (AM == kAttrChain && !wi) swk[e * NT + tid] = Wk;
+                if (kChain && !wi) swk[e * NT + tid] = Wk;
                 if (AM == kAttrSlot) {
                     const float g0 = __ldg(gp), g1 = C > 1 ? __ldg(gp + 1) : 0.0f, g2 = C > 2 ? __ldg(gp + 2) : 0.0f;
                     red_add_v4(a.ws.gcam + kGcamStride * (vb + g) + 8, 0.0f, Wk * g0, Wk * g1, Wk * g2);
@@ -298,31 +395,44 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     // it holds no per-slot registers
     const float inv2tau = 0.5f / tau;
     float gi0 = 0.0f, gi1 = 0.0f, gi2 = 0.0f;  // dL/dI of this pixel (kAttrChain)
-    if (AM == kAttrChain) {
+    if (kChain) {
         gi0 = __ldg(gp);
         if (C > 1) gi1 = __ldg(gp + 1);
         if (C > 2) gi2 = __ldg(gp + 2);
     }
-    for (int e = 0; e < n; ++e) {
-        const float4 J = jst[e * NT + tid];
-        float4 r0, r1, r2, r3;
-        const int64_t o = vb + __ldg(li + e);
-        load_rec(a.ws.rec, o, r0, r1, r2, r3);
-        const Trace tr = trace_px(r0, r1, r2, r3, px, py);
-        const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
-        const float er = sqrt_approx(0.5f * tr.b);
-        const float dqt = fmaf(J.w, inv2tau, -0.25f * ea * J.x);
-        const float db = J.z * rcp_approx(4.0f * er);
-        float gv[9];
-        chain_to_camera(a, o, tr, r3, px, py, invF, dqt, J.y, db, gv);
-        float* gc = a.ws.gcam + kGcamStride * o;
-        red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
-        red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
-        if (AM == kAttrChain) {
-            const float wk = wi ? __ldg(wi + e) : swk[e * NT + tid];
-            red_add_v4(gc + 8, gv[8], wk * gi0, wk * gi1, wk * gi2);
-        } else {
-            red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+    // two entries at a time: their ids, then both records and second records
+    for (int e0 = 0; e0 < n; e0 += 2) {
+        int64_t o[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) o[h] = vb + __ldg(li + min(e0 + h, n - 1));
+        float4 r[2][4], q[2][2];
+        float wk[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            load_rec(a.ws.rec, o[h], r[h][0], r[h][1], r[h][2], r[h][3]);
+            q[h][0] = __ldg(a.ws.rec2 + 2 * o[h]);
+            q[h][1] = __ldg(a.ws.rec2 + 2 * o[h] + 1);
+            const int e = min(e0 + h, n - 1);
+            wk[h] = kChain ? (wi ? __ldg(wi + e) : swk[e * NT + tid]) : 0.0f;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = e0 + h;
+            if (e < n) {
+                const float4 J = jst[e * NT + tid];
+                const Trace tr = trace_px(r[h][0], r[h][1], r[h][2], r[h][3], px, py);
+                const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
+                const float er = sqrt_approx(0.5f * tr.b);
+                const float dqt = fmaf(J.w, inv2tau, -0.25f * ea * J.x);
+                const float db = J.z * rcp_approx(4.0f * er);
+                float gv[9];
+                chain_to_camera(q[h][0], q[h][1], tr, r[h][3], invF, dqt, J.y, db, gv);
+                float* gc = a.ws.gcam + kGcamStride * o[h];
+                red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
+                red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
+                if (kChain) red_add_v4(gc + 8, gv[8], wk[h] * gi0, wk[h] * gi1, wk[h] * gi2);
+                else red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+            }
         }
     }
 }
@@ -353,6 +463,24 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : (KM <= 20 ? 4 : 3)) k_
         else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t, hb);
         else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t, hb);
         else backward_tile<KM, TH, kAttrSlot>(a, t, hb);
+    }
+}
+
+// The fitting step's backward (the forward's W_k supplied, C <= 3, lists of
+// up to 20): every tile takes the packed set-up.
+template <int KM>
+__global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
+    __shared__ int s_slot;
+    constexpr int TH = 8;
+    const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = atomicAdd(&a.hdr->counters[a.cls + kMaxClasses], 1);
+        __syncthreads();
+        const int tb = R * a.hdr->class_begin[a.cls] + s_slot;
+        __syncthreads();
+        if (tb >= R * a.hdr->class_end[a.cls]) return;
+        const int t = tb / R, hb = tb - t * R;
+        backward_tile<KM, TH, kAttrPacked>(a, t, hb);
     }
 }
 
@@ -436,7 +564,8 @@ __device__ __forceinline__ void backward_tile_generic(const Args& a, int t) {
         float4 r0, r1, r2, r3;
         load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
         const Trace tr = trace_px(r0, r1, r2, r3, px, py);
-        chain_to_camera(a, vb + li[k], tr, r3, px, py, invF, dqt, sk[5], db, gv);
+        const int64_t o = vb + li[k];
+        chain_to_camera(__ldg(a.ws.rec2 + 2 * o), __ldg(a.ws.rec2 + 2 * o + 1), tr, r3, invF, dqt, sk[5], db, gv);
         float* gc = a.ws.gcam + kGcamStride * (vb + li[k]);
         red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
         red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
@@ -565,9 +694,11 @@ static cudaError_t launch_tiles(Kern k, const char* name, int nblocks, int nthre
     return cudaPeekAtLastError();
 }
 
+// The stream, plus the W_k buffer where it fits (it holds W_k when the
+// backward recomputes them, dA_k when the forward's W_k are supplied).
 template <int KM, int TH>
-static size_t backward_smem_bytes(bool with_wk = true) {
-    return (size_t)KM * 16 * TH * (with_wk && wk_in_smem<KM, TH>() ? 20 : 16);
+static size_t backward_smem_bytes(bool = true) {
+    return (size_t)KM * 16 * TH * (wk_in_smem<KM, TH>() ? 20 : 16);
 }
 
 template <typename Kern>
@@ -599,6 +730,17 @@ static cudaError_t launch_backward_pair(const char* name, const char* wname, int
     if (e == cudaSuccess && (kinds & 2))
         e = launch_tiles(k_backward<KM, 8, true>, wname, nblocks, 128, backward_smem_bytes<KM, 8>(w), s, a);
     return e;
+}
+
+// The packed form (k_backward_packed) for capacities up to 20, when every
+// view brings the forward's weights and C <= 3.
+cudaError_t launch_backward_packed(int KM, int nblocks, cudaStream_t s, const Args& a) {
+    switch (KM) {
+        case 8: return launch_tiles(k_backward_packed<8>, "k_backward<8>", nblocks, 128, backward_smem_bytes<8, 8>(), s, a);
+        case 16: return launch_tiles(k_backward_packed<16>, "k_backward<16>", nblocks, 128, backward_smem_bytes<16, 8>(), s, a);
+        case 20: return launch_tiles(k_backward_packed<20>, "k_backward<20>", nblocks, 128, backward_smem_bytes<20, 8>(), s, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a0) {
