@@ -10,8 +10,13 @@ One step = one analysis-by-synthesis fitting iteration over 8 views of
 Every kernel in the step is this library's.  Metric: Mpix/s (pixels of all
 views rendered forward + backward per second, all ranks).
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
-bounded pixel sample of the same workload instead.
+Prints one JSON line.  Beyond the contract's keys it carries: Gaussian-ray
+evaluations per second (coarse-pass traces counted on the device), the
+forward and forward + backward of every workload shape (64^2 dense frame,
+256^2 feature scene, the 8-view step's scene, 1024^2 / 500k scene) fused and
+split, with pair rates against the measured pair ceilings; the serving load
+sweep; the sampler, pose-fitting and converter rows.  --impl reference times
+the FP64 CPU oracle on a bounded pixel sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -54,13 +59,13 @@ def workload_config(world=1):
 #             (voge_render_bwd_w), so the forward pair is not recomputed
 #             (it would add 24)
 # plus, per kept entry, 80 FLOP for the chain to camera space (backward only)
-# and, in the forward, 30 FLOP for the entry's coarse-pass ray trace (Eq. 6:
-# offsets 4, b and its numerator 11, qb 5, the threshold test 1, l 5) and its
-# fine-pass sigma and e^{q} (4).  Candidates the coarse pass traces and
-# rejects are not counted, so the forward figure is a lower bound.
+# and, in the forward, 30 FLOP for each Gaussian-ray trace of Eq. 6 (offsets
+# 4, b and its numerator 11, qb 5, the threshold test 1, l 5, sigma and e^{q}
+# 4): every coarse-pass trace (counted on the device, voge_render_stats) and
+# the fine pass's set-up trace of each kept entry.
 FLOP_PER_PAIR = {"fwd": 24, "bwd": 28}
 FLOP_PER_ENTRY_BWD = 80
-FLOP_PER_ENTRY_FWD = 30
+FLOP_PER_TRACE = 30
 # GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2070 MHz max SM clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -68,7 +73,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="voge", choices=["voge", "reference"])
     ap.add_argument("--seed", type=int, default=0)
@@ -77,7 +82,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--serving-seconds", type=float, default=4.0, help="measured seconds of each serving run")
+    ap.add_argument("--no-configs", action="store_true", help="skip the forward / fwd+bwd rows of the other workloads")
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-posefit", action="store_true")
     ap.add_argument("--no-converters", action="store_true")
@@ -340,14 +346,18 @@ def measured_hbm_gbs():
         return 6800.0
 
 
-def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
-    """Poisson render-and-compare requests (mean gap 2 ms) against resident scenes.
+def serving_bench(dev, seconds, batching, graphs, mean_gap_s=0.002, seed=0, warmup_s=0.5, max_queue=0):
+    """Poisson render-and-compare requests against resident scenes.
 
     Scene pool: for each attribute width C in {3, 16, 128}, four scenes with N
     drawn from U[1k, 100k] (the 8-view generator's distribution).  Each request
     picks side in {128, 256, 512}, K in {10, 20, 32}, a scene of its C and a
     random camera on the view sphere; it returns the loss and the gradients of
-    the means and the camera into pinned host memory."""
+    the means and the camera into pinned host memory.  batching: continuous
+    batching (else one request per tick); graphs: ticks replayed as CUDA
+    graphs.  max_queue > 0 bounds the pending queue: past saturation the
+    server turns requests away (counted as rejected) instead of building an
+    unbounded backlog."""
     import threading
 
     import torch
@@ -356,8 +366,8 @@ def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
     from paper_2205_15401_gb300 import voge
 
     rng = np.random.default_rng(seed)
-    srv = voge.Server(mem_budget_bytes=48 << 30, max_slots=256, use_graphs=batching, batching=batching,
-                      inflight_ticks=2 if batching else 1)
+    srv = voge.Server(mem_budget_bytes=48 << 30, max_slots=256, use_graphs=graphs, batching=batching,
+                      inflight_ticks=2 if batching else 1, max_queue=max_queue)
     pool = {}
     for C in (3, 16, 128):
         pool[C] = []
@@ -368,10 +378,11 @@ def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
     targets = {(side, C): torch.rand((side * side, C)).pin_memory() for side in (128, 256, 512) for C in (3, 16, 128)}
     out_pool = [{"grad_means": torch.empty((100_001, 3)).pin_memory(), "grad_cam": torch.empty(12).pin_memory(),
                  "loss": torch.empty(1).pin_memory()} for _ in range(512)]
-    stream = scenes.serving_stream(seed=seed, duration_s=warmup_s + seconds)
+    stream = scenes.serving_stream(seed=seed, duration_s=warmup_s + seconds, mean_gap_s=mean_gap_s)
     done, lock = [], threading.Lock()
     tickets = []
     cv = threading.Condition()
+    refused = [0]
 
     def consumer():
         k = 0
@@ -406,6 +417,8 @@ def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
             with cv:
                 tickets.append((t, side * side, req["t"]))
                 cv.notify()
+        elif req["t"] >= warmup_s:
+            refused[0] += 1
     with cv:
         tickets.append(None)
         cv.notify()
@@ -413,14 +426,153 @@ def serving_bench(dev, seconds, batching, seed=0, warmup_s=1.0):
     stats = srv.stats()
     srv.close()
     meas = [(tm, px) for arrive, tm, px, rc in done if rc == 0 and arrive >= warmup_s]
+    offered = sum(1 for req in stream if req["t"] >= warmup_s)
+    if not meas:
+        return {"requests": 0, "offered": offered, "rejected": refused[0]}
     lat = np.array([tm["done_us"] - tm["submit_us"] for tm, _ in meas]) / 1e3
     t_first = min(tm["submit_us"] for tm, _ in meas)
     t_last = max(tm["done_us"] for tm, _ in meas)
-    mpix = sum(px for _, px in meas) / ((t_last - t_first) / 1e6) / 1e6
-    return {"requests": len(meas), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "mpix_s": mpix, "ticks": stats["ticks"],
+    span = (t_last - t_first) / 1e6
+    return {"requests": len(meas), "offered": offered, "rejected": refused[0],
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "mpix_s": sum(px for _, px in meas) / span / 1e6,
+            "requests_per_s": len(meas) / span, "ticks": stats["ticks"],
             "requests_per_tick": stats["requests_in_ticks"] / max(stats["ticks"], 1),
-            "rejected": stats["rejected"], "graphs": stats["graphs_captured"]}
+            "graphs": stats["graphs_captured"]}
+
+
+def serving_suite(dev, seconds, seed=0):
+    """The serving workload (mean gap 2 ms) and a load sweep to past
+    saturation, each load with three arms: continuous batching with CUDA-graph
+    ticks; one request per tick with graph ticks (separates graph replay from
+    batching); one request per tick with plain launches (the per-request
+    comparator).  Past saturation the pending queue is bounded (256), so the
+    arms deliver what they can and turn the rest away."""
+    arms = (("batched", True, True), ("per_request_graphs", False, True), ("per_request_plain", False, False))
+    out = {"workload": "Poisson arrivals, 0.5 s warm-up then measured; N U[1k,100k] (resident scenes), side "
+                       "{128,256,512}, C {3,16,128}, K {10,20,32}; latency = submit to outputs in host memory",
+           "measured_s": seconds}
+    for gap_ms in (2.0, 1.0, 0.5, 0.25):
+        row = {}
+        for name, batching, graphs in arms:
+            row[name] = serving_bench(dev, seconds, batching, graphs, mean_gap_s=gap_ms / 1e3, seed=seed,
+                                      max_queue=256)
+        out[f"gap_{gap_ms:g}ms"] = row
+    # the configured workload's line: mean gap 2 ms
+    out["batched"] = out["gap_2ms"]["batched"]
+    out["plain"] = out["gap_2ms"]["per_request_plain"]
+    return out
+
+
+def _traced(voge, fn, reps):
+    """Run fn reps times with the library's kernel tracing on: (CUDA-event ms
+    per call, {kernel: ms per call})."""
+    import torch
+
+    voge.voge_trace_reset()
+    voge.voge_trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    voge.voge_trace_enable(False)
+    tr = voge.voge_trace_read()
+    return e0.elapsed_time(e1) / reps, {k: t / reps for k, (n, t) in tr.items() if n > 0}
+
+
+def _sum_ms(kms, prefixes):
+    return sum(t for k, t in kms.items() if k.startswith(prefixes))
+
+
+def workload_rows(voge, dev, alu, reps=20):
+    """Forward and forward + backward of every workload shape, each timed
+    alone: Mpix/s, Gaussian-ray evaluations per second, and each tile
+    kernel's pair rate against the measured pair ceilings and its FLOP rate
+    against the measured FMA rate.  The forward is also timed split (the
+    selection kernel, then the fine kernel over its lists: the fine pass
+    measured on its own, Eq. 7-8).  The backward takes the forward's weights
+    and a fixed N(0,1) image gradient.  Gaussian-ray evaluations: the coarse
+    pass's traces (counted on the device) plus one set-up trace per kept entry
+    in the forward, two per kept entry in the backward (set-up and chain)."""
+    import torch
+
+    from paper_2205_15401_gb300 import scenes
+
+    fma = alu["fma_tflops"] if alu else None
+    out = {}
+    for name, sc in (("plain_64", scenes.plain_64(seed=0)), ("posefit_256", scenes.posefit_256(seed=0)),
+                     ("fit_8x512", scenes.fit_8x512(seed=0)), ("large_1024", scenes.large_1024(seed=0))):
+        cams = scenes.cameras(sc, voge.voge_pose_to_RT)
+        N, C = sc["means"].shape[0], sc["attr"].shape[1]
+        m, p, a = (torch.tensor(sc[k], device=dev) for k in ("means", "inv_cov", "attr"))
+        row = {"N": N, "C": C, "K": sc["K"], "eta": sc["eta"], "views": len(cams),
+               "side": int(cams[0]["H"])}
+        for form, flags in (("fused", 0), ("split", voge.VOGE_FLAG_SPLIT_FORWARD)):
+            r = voge.Renderer(cams, N, C, K=sc["K"], tau=sc["tau"], thresh=sc["eta"], flags=flags, device=dev)
+            img, w, idx = r.alloc_outputs()
+            g_img = torch.randn(img.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+            gm, gp, ga = torch.zeros_like(m), torch.zeros_like(p), torch.zeros_like(a)
+            gc = torch.zeros((len(cams), 12), device=dev)
+
+            def fwd():
+                r.forward(m, p, a, out=(img, w, idx))
+
+            def fwd_bwd():
+                r.forward(m, p, a, out=(img, w, idx))
+                r.backward(m, p, a, idx, g_img, gm, gp, ga, gc, weights=w)
+
+            for _ in range(3):
+                fwd_bwd()
+            fwd()
+            st = voge.voge_render_stats(r.workspace)
+            ms_f, k_f = _traced(voge, fwd, reps)
+            ms_fb, k_fb = _traced(voge, fwd_bwd, reps)
+            P, T, E, pairs = r.pixels, st["traces"], st["entries"], st["pairs"]
+            f = {"ms_fwd": ms_f, "ms_fwd_bwd": ms_fb, "mpix_s_fwd": P / ms_f / 1e3,
+                 "mpix_s_fwd_bwd": P / ms_fb / 1e3, "kernels_fwd": k_f,
+                 "gaussian_ray_evals_per_s": {"fwd": (T + E) / (ms_f / 1e3), "fwd_bwd": (T + 3 * E) / (ms_fb / 1e3)}}
+            if form == "fused":
+                row.update({"pixels": P, "coarse_traces": T, "entries": E, "pairs": pairs})
+            ms_pairs_f = _sum_ms(k_f, ("k_render", "k_fine"))
+            if ms_pairs_f > 0:
+                f["fwd_pair_kernel_gpairs"] = pairs / ms_pairs_f / 1e6
+                if alu:
+                    f["fwd_pair_frac"] = f["fwd_pair_kernel_gpairs"] / alu["fwd_gpairs"]
+            if form == "fused" and fma:
+                ms_r = _sum_ms(k_f, ("k_render",))
+                if ms_r > 0:
+                    tf = (pairs * FLOP_PER_PAIR["fwd"] + (T + E) * FLOP_PER_TRACE) / ms_r / 1e9
+                    f["render_tflops"] = tf
+                    f["render_frac_of_measured_fma"] = tf / fma
+            if form == "split":
+                ms_fine = _sum_ms(k_f, ("k_fine",))
+                ms_sel = _sum_ms(k_f, ("k_select",))
+                f["select_ms"], f["fine_ms"] = ms_sel, ms_fine
+                if ms_fine > 0:
+                    f["fine_gpairs"] = pairs / ms_fine / 1e6
+                    f["fine_tflops"] = (pairs * FLOP_PER_PAIR["fwd"] + E * FLOP_PER_TRACE) / ms_fine / 1e9
+                    if alu:
+                        f["fine_frac_of_pair_ceiling"] = f["fine_gpairs"] / alu["fwd_gpairs"]
+                    if fma:
+                        f["fine_frac_of_measured_fma"] = f["fine_tflops"] / fma
+            ms_b = _sum_ms(k_fb, ("k_backward",))
+            if form == "fused" and ms_b > 0:
+                f["bwd_kernel_ms"] = ms_b
+                f["bwd_gpairs"] = pairs / ms_b / 1e6
+                tf = (pairs * FLOP_PER_PAIR["bwd"] + E * FLOP_PER_ENTRY_BWD) / ms_b / 1e9
+                f["bwd_tflops"] = tf
+                if alu:
+                    f["bwd_pair_frac"] = f["bwd_gpairs"] / alu["bwd_gpairs"]
+                if fma:
+                    f["bwd_frac_of_measured_fma"] = tf / fma
+            row[form] = f
+            del r, img, w, idx, g_img
+        out[name] = row
+        torch.cuda.empty_cache()
+    return out
 
 
 # --------------------------------------------------------------- GPU path ---
@@ -445,7 +597,8 @@ KERNEL_SOURCES = ("voge_api.cu", "voge_backward.cu", "voge_device.cuh", "voge_fo
 
 # The kernels of the forward pass (projection, binning, tile sort, render) and
 # of the backward pass (adjoint, gradient finalisation, pose chain) by name.
-FWD_KERNELS = ("k_project", "k_tile_totals", "k_scan_tiles", "k_scatter", "k_sort_tiles", "k_render")
+FWD_KERNELS = ("k_project", "k_tile_totals", "k_scan_tiles", "k_scatter", "k_sort_tiles", "k_render", "k_select",
+               "k_fine")
 BWD_KERNELS = ("k_backward", "k_grad_finalize", "k_pose_grad")
 
 
@@ -573,10 +726,25 @@ def main():
     launches = sum(n for n, _ in trace.values())
     passes = pass_throughput(trace, P, args.steps)
 
+    # ------------------------------------------------ measured ALU ceilings
+    # Register-only loops of the FMA, ex2 and both pair terms on this GPU: the
+    # measured peak of the roofline, and the speed-of-light of the pair loops.
+    alu = None if args.no_alu_ceilings else voge.voge_measure_alu_peaks()
+    torch.cuda.synchronize()
+
+    # ------------------------------------------------ what one step's forward did
+    r.forward(means, inv_cov, attr, out=(image, weights, index))
+    st = voge.voge_render_stats(r.workspace)
+    pairs, entries, traces = float(st["pairs"]), float(st["entries"]), float(st["traces"])
+    step_s = ms_max / args.steps / 1e3
+    ray_evals = {"coarse_traces_per_step": traces, "entries_per_step": entries, "pairs_per_step": pairs,
+                 "fwd_bwd_per_s": (traces + 3 * entries) / step_s,
+                 "what": "Gaussian-ray evaluations (Eq. 6): the coarse pass's traces (counted on the device) + one "
+                         "set-up trace per kept entry (forward) + two per kept entry (backward set-up and chain)"}
+    if passes and "fwd" in passes:
+        ray_evals["fwd_per_s"] = (traces + entries) / (passes["fwd"]["ms_per_step"] / 1e3)
+
     # ------------------------------------------------ roofline of the top kernel
-    cnt = (index[:, : r.L] >= 0).sum(1).to(torch.float64)
-    pairs = float((cnt * cnt).sum().item())
-    entries = float(cnt.sum().item())
     top = max(trace.items(), key=lambda kv: kv[1][1]) if trace else (None, (0, 0.0))
     top_name, (top_n, top_ms) = top
     roofline = None
@@ -585,26 +753,22 @@ def main():
         if top_name.startswith("k_backward"):
             flop = pairs * FLOP_PER_PAIR["bwd"] + entries * FLOP_PER_ENTRY_BWD
         elif top_name.startswith("k_render"):
-            flop = pairs * FLOP_PER_PAIR["fwd"] + entries * FLOP_PER_ENTRY_FWD
+            flop = pairs * FLOP_PER_PAIR["fwd"] + (traces + entries) * FLOP_PER_TRACE
         else:
             flop = None
         if flop is not None:
             ach = flop / avg_s / 1e12
-            roofline = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                        "traffic": profiled_traffic(top_name, kernel_source_hash()),
-                        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                        "avg_launch_ms": top_ms / top_n, "pairs_per_launch": pairs}
+            measured = alu is not None and alu["fma_tflops"] > 0
+            peak = alu["fma_tflops"] if measured else FP32_PEAK_TFLOPS
+            roofline = {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "traffic": profiled_traffic(top_name, kernel_source_hash()),
+                        "peak_source": "measured: FP32 FMA register loop on every SM, this run (of measured)"
+                        if measured else "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                        "peak_derived": FP32_PEAK_TFLOPS, "avg_launch_ms": top_ms / top_n,
+                        "flop_per_launch": flop, "pairs_per_launch": pairs}
     kernels = {k: {"launches": n, "ms_per_launch": t / max(n, 1), "share": t / max(sum(x for _, x in trace.values()),
                                                                                   1e-30)}
                for k, (n, t) in trace.items()}
-
-    # ------------------------------------------------ measured ALU ceilings
-    # Register-only loops of the FMA, ex2 and both pair terms on this GPU: the
-    # measured counterpart of the derived peak, and the speed-of-light of the
-    # pair loops (algorithmic pairs per second of each tile kernel against it).
-    alu = None if args.no_alu_ceilings else voge.voge_measure_alu_peaks()
-    torch.cuda.synchronize()
     pair_frac = {}
     for side, prefix, key in (("fwd", "k_render", "fwd_gpairs"), ("bwd", "k_backward", "bwd_gpairs")):
         ent = [(k, n, t) for k, (n, t) in trace.items() if k.startswith(prefix) and n > 0]
@@ -616,31 +780,23 @@ def main():
         "fma_tflops": alu["fma_tflops"], "ex2_tops": alu["ex2_tops"], "fwd_gpairs": alu["fwd_gpairs"],
         "bwd_gpairs": alu["bwd_gpairs"], "pairs": pair_frac,
         "how": "voge_measure_alu_peaks: register-only loops on every SM, CUDA events"}
-    if roofline is not None and alu and alu["fma_tflops"] > 0:
-        roofline["peak_measured"] = alu["fma_tflops"]
-        roofline["frac_of_measured"] = roofline["achieved"] / alu["fma_tflops"]
 
     # ------------------------------------------------ e2e through host buffers
+    # The same step as the timed one (forward, MSE, backward, Adam) through the
+    # public API, with the parameters and targets copied in from pinned host
+    # memory and the loss and updated parameters copied back, every step.
     e2e = None
     if not args.no_e2e:
         h_par = torch.tensor(host_par).pin_memory()
         h_target = target.cpu().pin_memory()
-        h_grad = torch.empty(n_par).pin_memory()
-        h_gcam = torch.empty((W["views"], 12)).pin_memory()
+        h_out = torch.empty(n_par).pin_memory()
         h_loss = torch.empty(1).pin_memory()
 
         def e2e_step():
             par.copy_(h_par, non_blocking=True)
             target.copy_(h_target, non_blocking=True)
-            r.forward(means, inv_cov, attr, out=(image, weights, index))
-            loss.zero_()
-            voge.voge_mse_grad(image, target, g_image, loss)
-            grad.zero_()
-            g_cam.zero_()
-            r.backward(means, inv_cov, attr, index, g_image, g_means, g_inv_cov, g_attr, g_cam,
-                       reuse_projection=True, weights=weights)
-            h_grad.copy_(grad, non_blocking=True)
-            h_gcam.copy_(g_cam, non_blocking=True)
+            step()
+            h_out.copy_(par, non_blocking=True)
             h_loss.copy_(loss, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             return float(h_loss[0])
@@ -655,8 +811,10 @@ def main():
         t_e2e, _ = reduce_over_ranks(time.perf_counter() - t0, 0, world, dev)
         e2e = {"value": pix_all / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (n_par + target.numel())),
-               "d2h_bytes_per_step": int(4 * (n_par + g_cam.numel() + 1)),
-               "ms_per_step": 1e3 * t_e2e / args.steps}
+               "d2h_bytes_per_step": int(4 * (n_par + 1)),
+               "ms_per_step": 1e3 * t_e2e / args.steps,
+               "what": "forward + MSE + backward + Adam as the timed step; parameters and targets in, loss and "
+                       "updated parameters out, synchronised every step"}
 
     # ------------------------------------------------ plain comparator
     plain = None
@@ -674,7 +832,7 @@ def main():
 
         plain_step()
         torch.cuda.synchronize()
-        k_plain = 2
+        k_plain = 10
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(k_plain):
@@ -687,11 +845,11 @@ def main():
 
     serving = None
     if rank == 0 and not args.no_serving:
-        batched = serving_bench(dev, args.serving_seconds, True, seed=args.seed)
-        plain_srv = serving_bench(dev, args.serving_seconds, False, seed=args.seed)
-        serving = {"workload": "Poisson arrivals, mean gap 2 ms, 1 s warm-up then measured; N U[1k,100k] "
-                               "(resident scenes), side {128,256,512}, C {3,16,128}, K {10,20,32}",
-                   "batched": batched, "plain": plain_srv}
+        serving = serving_suite(dev, args.serving_seconds, seed=args.seed)
+
+    workloads = None
+    if rank == 0 and not args.no_configs:
+        workloads = workload_rows(voge, dev, alu)
 
     # ------------------------------------------------ neural sampler (Sec. 3.4 Eq. 10)
     sampler = None
@@ -719,6 +877,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": workload_config(world),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+               "gaussian_ray_evals": ray_evals, "workloads": workloads,
                "serving": serving, "sampler": sampler, "posefit": posefit, "converters": converters,
                "clocks": clk, "kernels": kernels, "passes": passes, "alu_ceilings": alu_ceilings, "loss": float(loss.item())}
         print(json.dumps(out))

@@ -132,6 +132,26 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
                     size_t workspace_bytes, voge_stream_t stream);
 
 /*
+ * What the last forward pass run in a workspace did, counted on the device
+ * while it ran (one addition per warp and tile):
+ *   traces   Gaussian-ray traces of the coarse pass: evaluations of Eq. 6
+ *            (l, e^{q}, sigma) for a (pixel, candidate kernel), including the
+ *            candidates the threshold or the list then rejects
+ *   entries  kept (pixel, kernel) entries: the sum of the list lengths
+ *   pairs    (k, j) pairs of the fine pass's transmittance sums (Eq. 7): the
+ *            sum over pixels of the squared list length
+ * `workspace` is the one passed to voge_render_fwd; the counts stay valid
+ * until the next call that uses the workspace (voge_render_bwd resets them).
+ * Copies 24 bytes to `out` (host) on `stream` and waits for the stream.
+ * VOGE_ERR_ARG for NULL or misaligned pointers, VOGE_ERR_CUDA on a CUDA failure.
+ * Not a step of the paper: an aid for measurement.
+ */
+typedef struct {
+    int64_t traces, entries, pairs;
+} voge_render_stats_t;
+int voge_render_stats(const void* workspace, voge_render_stats_t* out, voge_stream_t stream);
+
+/*
  * Fine pass alone (Eq. 7 and 8) over given per-pixel lists: for each pixel
  * with list S_p (the entries before the first slot outside [0, N)),
  *   A_k = sum_{j in S_p} (a_j/2)(1 + erf((l_k - l_j) sqrt(b_j/2))),

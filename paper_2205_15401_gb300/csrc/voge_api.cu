@@ -1,6 +1,7 @@
 // voge_api.cu -- the C ABI of libvoge.so (declared in include/voge.h):
 // argument checks, workspace layout and the launch sequence of one render.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <mutex>
@@ -485,6 +486,20 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
     if ((grad_means || grad_inv_cov || grad_cam || grad_attr) &&
         launch_grad_finalize(record_grid(p->N), p->B, p->N, 1, s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
+    return VOGE_OK;
+}
+
+int voge_render_stats(const void* workspace, voge_render_stats_t* out, voge_stream_t stream_) {
+    if (!workspace || !out || (reinterpret_cast<uintptr_t>(workspace) & 255)) return VOGE_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    unsigned long long c[3] = {0, 0, 0};
+    // the call header sits at the start of every workspace layout
+    const char* h = static_cast<const char*>(workspace) + offsetof(BatchHdr, traces);
+    if (cudaMemcpyAsync(c, h, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOGE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOGE_ERR_CUDA;
+    out->traces = (int64_t)c[0];
+    out->entries = (int64_t)c[1];
+    out->pairs = (int64_t)c[2];
     return VOGE_OK;
 }
 

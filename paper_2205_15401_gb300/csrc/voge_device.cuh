@@ -99,6 +99,10 @@ struct BatchHdr {
                                        // standalone fine pass)
     int32_t shared_scene;   // 1: every view renders the same Gaussians (records rec_base = v * N)
     int32_t pad[1];
+    // what the forward pass of this call did (voge_render_stats): Gaussian-ray
+    // traces of the coarse pass (Eq. 6 evaluations), kept entries, and the
+    // fine pass's (k, j) pairs (sum over pixels of n_p^2)
+    unsigned long long traces, entries, pairs, pad2;
 };
 static_assert(sizeof(BatchHdr) % 16 == 0, "BatchHdr layout");
 

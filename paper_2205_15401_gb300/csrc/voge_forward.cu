@@ -354,6 +354,7 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
     int n = 0;
     float lk_last = -INFINITY, kbar = INFINITY;
     int32_t li_last = INT32_MIN;
+    unsigned traced = 0;  // candidates this pixel traced (Eq. 6)
 
     const TileSrc src = tile_source<NT>(a, vd, t);
     if (src.count == 0) {
@@ -450,6 +451,7 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
                 }
                 const float4 r0 = stage[q], r1 = stage[NT + q], r2 = stage[2 * NT + q];
                 const float l = candidate_key(r0, r1, r2, r3, px, py, Qeta);
+                ++traced;
                 if (!(l > 0.0f)) continue;
                 const int32_t g = sgid[q];
                 const bool full = n == K;
@@ -497,6 +499,17 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             }
         }
         if (__syncthreads_and(!active)) break;
+    }
+    // the call's counts: one addition per warp
+    {
+        const unsigned w_traced = __reduce_add_sync(0xffffffffu, traced);
+        const unsigned w_entries = __reduce_add_sync(0xffffffffu, (unsigned)n);
+        const unsigned w_pairs = __reduce_add_sync(0xffffffffu, (unsigned)(n * n));
+        if ((tid & 31) == 0) {
+            atomicAdd(&a.hdr->traces, (unsigned long long)w_traced);
+            atomicAdd(&a.hdr->entries, (unsigned long long)w_entries);
+            atomicAdd(&a.hdr->pairs, (unsigned long long)w_pairs);
+        }
     }
     // The lists are sorted; the selection buffers are free from here on.
     // Each warp holds two 16-pixel row segments of the tile (lanes 0-15 and
@@ -705,6 +718,7 @@ __device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
     float* lk = a.ws.gkey + gpix * (int64_t)a.ws.gen_L * 8;
     int32_t* li = a.ws.gid + gpix * (int64_t)a.ws.gen_L;
     int n = 0;
+    unsigned traced = 0;  // candidates this pixel traced (Eq. 6)
 
     const TileSrc src = tile_source<NT>(a, vd, t);
     bool active = valid;
@@ -739,6 +753,7 @@ __device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
                     break;
                 }
                 const float l = candidate_key(stage[q], stage[NT + q], stage[2 * NT + q], r3, px, py, vd.Qeta);
+                ++traced;
                 if (l > 0.0f) {
                     const int32_t g = sgid[q];
                     if (n < L || l < lk[L - 1] || (l == lk[L - 1] && g < li[L - 1])) {
@@ -756,6 +771,16 @@ __device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
             }
         }
         if (__syncthreads_and(!active)) break;
+    }
+    {
+        const unsigned w_traced = __reduce_add_sync(0xffffffffu, traced);
+        const unsigned w_entries = __reduce_add_sync(0xffffffffu, (unsigned)n);
+        const unsigned w_pairs = __reduce_add_sync(0xffffffffu, (unsigned)(n * n));
+        if ((tid & 31) == 0) {
+            atomicAdd(&a.hdr->traces, (unsigned long long)w_traced);
+            atomicAdd(&a.hdr->entries, (unsigned long long)w_entries);
+            atomicAdd(&a.hdr->pairs, (unsigned long long)w_pairs);
+        }
     }
     if (valid) {
         // fine pass with both loops over the list in global memory (L1 resident)

@@ -5,8 +5,8 @@
 // the current device:
 //   - the FP32 FMA rate (eight independent chains per thread),
 //   - the MUFU ex2.approx rate,
-//   - the rate of the forward pair term exactly as k_render evaluates it
-//     (u, erf by A&S 7.1.28, the signed accumulation into A_k),
+//   - the rate of the forward pair term exactly as the fine pass evaluates
+//     it (u, erf by A&S 7.1.28, A_k += copysign(m_j, u) erf|u|),
 //   - the rate of the backward pair adjoint exactly as k_backward evaluates
 //     it (A&S 7.1.26 with e^{-u^2}, the four accumulations).
 // The pair loops keep the k side in registers like the tile kernels and
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(256, 4) k_peak_ex2(int iters, float seed) {
     if (s == -1.2345678f) g_peak_sink = s;
 }
 
-// Forward pair term: the k_render<20, 16> occupancy (two CTAs of 256 per SM).
-__global__ void __launch_bounds__(256, 2) k_peak_pair_fwd(int iters, float seed) {
+// Forward pair term: the k_render<20, 16> occupancy (three CTAs of 256 per SM).
+__global__ void __launch_bounds__(256, 3) k_peak_pair_fwd(int iters, float seed) {
     float hi[kPairKM], lo[kPairKM], A[kPairKM];
 #pragma unroll
     for (int s = 0; s < kPairKM; ++s) {
@@ -75,9 +75,7 @@ __global__ void __launch_bounds__(256, 2) k_peak_pair_fwd(int iters, float seed)
 #pragma unroll
         for (int s = 0; s < kPairKM; ++s) {
             const float u = ((hi[s] - J.x) + (lo[s] - J.y)) * J.z;
-            const float q = erfc_as28(fabsf(u));
-            const float sm = copysignf(J.w, u);
-            A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
+            A[s] = fmaf(copysignf(J.w, u), 1.0f - erfc_as28(fabsf(u)), A[s]);
         }
         J.x = fmaf(J.x, 0.9999f, 1.5e-4f);  // the next j (drifts towards 1.5)
     }
@@ -161,20 +159,20 @@ extern "C" int voge_measure_alu_peaks(voge_alu_peaks* out, voge_stream_t stream)
     out->sms = nsm;
     const float seed = 0.5f;
     float ms[4] = {0, 0, 0, 0};
-    const int g4 = 4 * nsm, g2 = 2 * nsm;
+    const int g4 = 4 * nsm, g3 = 3 * nsm;
     cudaError_t e = timed([&] { k_peak_fma<<<g4, 256, 0, s>>>(kFmaIters, seed); }, s, &ms[0]);
     if (e == cudaSuccess) e = timed([&] { k_peak_ex2<<<g4, 256, 0, s>>>(kEx2Iters, seed); }, s, &ms[1]);
-    if (e == cudaSuccess) e = timed([&] { k_peak_pair_fwd<<<g2, 256, 0, s>>>(kFwdIters, seed); }, s, &ms[2]);
+    if (e == cudaSuccess) e = timed([&] { k_peak_pair_fwd<<<g3, 256, 0, s>>>(kFwdIters, seed); }, s, &ms[2]);
     if (e == cudaSuccess) e = timed([&] { k_peak_pair_bwd<<<g4, 128, 0, s>>>(kBwdIters, seed); }, s, &ms[3]);
     if (e != cudaSuccess) return VOGE_ERR_CUDA;
     for (int i = 0; i < 4; ++i) {
         if (!(ms[i] > 0.0f)) return VOGE_ERR_CUDA;
         out->ms[i] = ms[i];
     }
-    const double t256x4 = 256.0 * g4, t256x2 = 256.0 * g2, t128x4 = 128.0 * g4;
+    const double t256x4 = 256.0 * g4, t256x3 = 256.0 * g3, t128x4 = 128.0 * g4;
     out->fma_tflops = t256x4 * kFmaIters * 128.0 * 2.0 / (ms[0] * 1e-3) / 1e12;
     out->ex2_tops = t256x4 * kEx2Iters * 128.0 / (ms[1] * 1e-3) / 1e12;
-    out->fwd_gpairs = t256x2 * kFwdIters * (double)kPairKM / (ms[2] * 1e-3) / 1e9;
+    out->fwd_gpairs = t256x3 * kFwdIters * (double)kPairKM / (ms[2] * 1e-3) / 1e9;
     out->bwd_gpairs = t128x4 * kBwdIters * (double)kPairKM / (ms[3] * 1e-3) / 1e9;
     return VOGE_OK;
 }

@@ -46,6 +46,10 @@ class voge_alu_peaks(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
+class voge_render_stats_t(ctypes.Structure):
+    _fields_ = [("traces", ctypes.c_int64), ("entries", ctypes.c_int64), ("pairs", ctypes.c_int64)]
+
+
 class voge_params(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("tau", ctypes.c_float), ("thresh", ctypes.c_float), ("flags", ctypes.c_int32),
@@ -70,6 +74,8 @@ def lib():
             L.voge_workspace_bytes.restype = ctypes.c_size_t
             L.voge_render_fwd.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
             L.voge_render_fwd.restype = ctypes.c_int
+            L.voge_render_stats.argtypes = [vp, P(voge_render_stats_t), vp]
+            L.voge_render_stats.restype = ctypes.c_int
             L.voge_render_fine.argtypes = [P(voge_camera), P(voge_params), vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
                                            vp]
             L.voge_render_fine.restype = ctypes.c_int
@@ -176,6 +182,14 @@ def voge_render_fwd(cams, params, means, inv_cov, attr, image, weights, index, w
                                _ptr(image, f32), _ptr(weights, f32), _ptr(index, i32), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "voge_render_fwd")
+
+
+def voge_render_stats(workspace, stream=None):
+    """Counts of the last forward pass run in ``workspace``: a dict of
+    traces (coarse-pass Gaussian-ray traces), entries and pairs."""
+    st = voge_render_stats_t()
+    _check(lib().voge_render_stats(_ptr(workspace), ctypes.byref(st), _stream(stream)), "voge_render_stats")
+    return {"traces": int(st.traces), "entries": int(st.entries), "pairs": int(st.pairs)}
 
 
 def voge_render_fine(cams, params, means, inv_cov, attr, index, image, weights, workspace, stream=None):

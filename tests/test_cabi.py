@@ -98,6 +98,10 @@ def test_invalid_arguments_rejected_without_launch(voge):
     assert rc == -1  # no image
     rc = L.voge_render_fine(cams, ctypes.byref(p_bad), fake, fake, fake, fake, fake, None, fake, 1 << 30, None)
     assert rc == -1
+    st = voge.voge_render_stats_t()
+    assert L.voge_render_stats(None, ctypes.byref(st), None) == -1  # no workspace
+    assert L.voge_render_stats(fake, None, None) == -1  # no output
+    assert L.voge_render_stats(ctypes.c_void_p(260), ctypes.byref(st), None) == -1  # misaligned workspace
     p_long = voge.make_params(2, 100, 3, 40, 1.0, 0.01)
     rc = L.voge_render_fine(cams, ctypes.byref(p_long), fake, fake, fake, fake, fake, None, fake, 1 << 30, None)
     assert rc == -4  # lists longer than 32: VOGE_ERR_UNSUPPORTED, before any CUDA call

@@ -127,3 +127,26 @@ def test_fine_on_large_1024_lists():
     ref = oracle.fine(cams, m, p, a, 1.0, pix, idx[rows])
     assert np.abs(img2[rows] - ref["image"]).max() <= TOL_IMAGE
     assert np.abs(w2[rows] - ref["weights"]).max() <= TOL_IMAGE
+
+
+def test_render_stats_counts_match_the_lists():
+    """voge_render_stats: the kept entries and the fine pass's pairs equal the
+    counts of the index output exactly; the coarse pass traced at least every
+    kept entry, and the tiled path (depth-sorted, with early exit) traced no
+    more candidates than the plain path, which tests every Gaussian."""
+    voge = lib_ready()
+    from paper_2205_15401_gb300.voge import VOGE_FLAG_PLAIN
+
+    sc = scenes.fit_8x512(seed=31, N=6000, B=2, side=160)
+    cams, m, p, a = scene_inputs(sc)
+    traced = {}
+    for flags in (0, VOGE_FLAG_PLAIN):
+        r = voge.Renderer(cams, m.shape[0], 3, K=20, tau=1.0, thresh=0.01, flags=flags)
+        img, w, idx = r.forward(to_dev(m), to_dev(p), to_dev(a))
+        st = voge.voge_render_stats(r.workspace)
+        n = (idx[:, : r.L] >= 0).sum(1).to(torch.int64)
+        assert st["entries"] == int(n.sum()) > 0
+        assert st["pairs"] == int((n * n).sum())
+        assert st["traces"] >= st["entries"]
+        traced[flags] = st["traces"]
+    assert traced[0] <= traced[VOGE_FLAG_PLAIN]
