@@ -20,6 +20,8 @@ cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, c
 cudaError_t launch_backward_packed(int KM, int nblocks, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int render_blocks_per_sm(int KM, int fine);
+cudaError_t launch_render_generic(int64_t total_pixels, cudaStream_t s, const Args& a);
+cudaError_t launch_backward_generic(int64_t total_pixels, cudaStream_t s, const Args& a);
 int backward_blocks_per_sm(int KM);
 
 // Persistent tile launches: as many CTAs as can be resident at once (cached
@@ -401,6 +403,7 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
     int rc = upload_and_project(cams, p, l, a, b, 1, 1, s);
     if (rc != VOGE_OK) return rc;
     if (l.total_tiles == 0) return VOGE_OK;
+    if (l.KM == 0) return launch_render_generic(l.pixels, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
     if (!split)
         return launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a, 1) == cudaSuccess ? VOGE_OK
                                                                                                      : VOGE_ERR_CUDA;
@@ -478,8 +481,10 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
     if (l.total_tiles > 0) {
         const bool packed = weights && p->C <= 3 && l.KM > 0 && l.KM <= 20;
         const cudaError_t e =
-            packed ? launch_backward_packed(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a)
-                   : launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), weights ? 0 : 1, p->C >= 8 ? 2 : 1, s, a);
+            l.KM == 0 ? launch_backward_generic(l.pixels, s, a)
+            : packed  ? launch_backward_packed(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a)
+                      : launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), weights ? 0 : 1,
+                                              p->C >= 8 ? 2 : 1, s, a);
         if (e != cudaSuccess) return VOGE_ERR_CUDA;
     }
     // the finalize also folds in attribute gradients of up to three channels

@@ -23,37 +23,6 @@ namespace voge {
 
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
-// Camera-space gradient of one (pixel, kept Gaussian) pair: out[0..2] = dM,
-// out[3..8] = G (xx, xy, xz, yy, yz, zz) with entries of P treated as independent.
-// s0, s1: the pair's second record (camera-space P and centre ray).
-__device__ __forceinline__ void chain_to_camera(const float4& s0, const float4& s1, const Trace& t, const float4& r3,
-                                                float invF, float dqt, float dl, float db, float out[9]) {
-    const float ib = rcp_approx(t.b);
-    const float Mz = r3.y;
-    const float dlt = -Mz * t.num * ib;  // l - Mz
-    const float dx = t.du * invF, dy = t.dv * invF;
-    const float D0 = s1.z + dx, D1 = s1.w + dy;  // D = (D0, D1, 1)
-    // V = M - l D = -Mz D' - (l - Mz) D
-    const float V0 = fmaf(-Mz, dx, -dlt * D0), V1 = fmaf(-Mz, dy, -dlt * D1), V2 = -dlt;
-    const float Pxx = s0.x, Pxy = s0.y, Pxz = s0.z, Pyy = s0.w, Pyz = s1.x, Pzz = s1.y;
-    const float PV0 = fmaf(Pxx, V0, fmaf(Pxy, V1, Pxz * V2));
-    const float PV1 = fmaf(Pxy, V0, fmaf(Pyy, V1, Pyz * V2));
-    const float PV2 = fmaf(Pxz, V0, fmaf(Pyz, V1, Pzz * V2));
-    const float PD0 = fmaf(Pxx, D0, fmaf(Pxy, D1, Pxz));
-    const float PD1 = fmaf(Pxy, D0, fmaf(Pyy, D1, Pyz));
-    const float PD2 = fmaf(Pxz, D0, fmaf(Pyz, D1, Pzz));
-    const float q2 = 2.0f * dqt, lb = dl * ib, lh = 0.5f * lb;
-    out[0] = fmaf(q2, PV0, lb * PD0);
-    out[1] = fmaf(q2, PV1, lb * PD1);
-    out[2] = fmaf(q2, PV2, lb * PD2);
-    out[3] = fmaf(dqt, V0 * V0, fmaf(lb, V0 * D0, db * D0 * D0));
-    out[4] = fmaf(dqt, V0 * V1, fmaf(lh, fmaf(V0, D1, D0 * V1), db * D0 * D1));
-    out[5] = fmaf(dqt, V0 * V2, fmaf(lh, fmaf(V0, 1.0f, D0 * V2), db * D0));
-    out[6] = fmaf(dqt, V1 * V1, fmaf(lb, V1 * D1, db * D1 * D1));
-    out[7] = fmaf(dqt, V1 * V2, fmaf(lh, fmaf(V1, 1.0f, D1 * V2), db * D1));
-    out[8] = fmaf(dqt, V2 * V2, fmaf(lb, V2, db));
-}
-
 // How a tile adds the attribute gradient dL/dc_g += W_k dL/dI:
 //   kAttrLane:  one reduction per lane and channel (4 <= C < 8),
 //   kAttrWarp:  warp-cooperative rows, lanes over (source pixel, channel) (C >= 8),
@@ -484,104 +453,6 @@ __global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
     }
 }
 
-// Generic backward for list lengths above the register lists (L > 32).
-// Per-pixel scratch in the workspace: [L][8] floats = hi, lo, r, m, A->dA, dl, dm, dr.
-__device__ __forceinline__ void backward_tile_generic(const Args& a, int t) {
-    constexpr int TH = 16;
-    const int v = view_of_tile(a.views, a.hdr->nviews, t);
-    const ViewDesc& vd = a.views[v];
-    const int lt = t - vd.tile_base;
-    const int tiles_x = vd.tiles_x;
-    const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = vd.H, W = vd.W;
-    const float invF = vd.invF;
-    const int tid = threadIdx.x;
-    const int j = tx * kTileW + (tid & 15);
-    const int i = ty * TH + (tid >> 4);
-    if (i >= H || j >= W) return;
-    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = (int64_t)i * W + j;
-    const int64_t vb = vd.rec_base;
-    const int L = vd.L, C = vd.C;
-    const float tau = vd.tau;
-    const int32_t* li = vd.index_in + pix * L;
-    float* S = a.ws.gkey + (vd.pix_base + pix) * (int64_t)a.ws.gen_L * 8;
-    int n = 0;
-    while (n < L) {
-        const int32_t g = li[n];
-        if (g < 0 || g >= vd.N) break;
-        float4 r0, r1, r2, r3;
-        load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
-        const Entry e = entry_px(r0, r1, r2, r3, px, py);
-        float* s = S + 8 * n;
-        s[0] = e.hi; s[1] = e.lo; s[2] = e.r; s[3] = 0.5f * e.a;
-        s[4] = 0.0f; s[5] = 0.0f; s[6] = 0.0f; s[7] = 0.0f;
-        ++n;
-    }
-    const float* gp = vd.grad_image + pix * C;
-    for (int k = 0; k < n; ++k) {
-        float* sk = S + 8 * k;
-        float A = 0.0f;
-        for (int jj = 0; jj < n; ++jj) {
-            const float* sj = S + 8 * jj;
-            const float u = ((sk[0] - sj[0]) + (sk[1] - sj[1])) * sj[2];
-            const float q = erfc_as28(fabsf(u));
-            const float sm = copysignf(sj[3], u);
-            A = fmaf(-sm, q, A + (sj[3] + sm));
-        }
-        const float Wk = ex2_approx(-tau * kLog2e * A) * (2.0f * sk[3]);
-        const int32_t g = li[k];
-        float G = 0.0f;
-        for (int c = 0; c < C; ++c) {
-            const float gc = gp[c];
-            G = fmaf(gc, __ldg(vd.attr + (int64_t)g * C + c), G);
-            if (vd.grad_attr) atomicAdd(vd.grad_attr + (int64_t)g * C + c, Wk * gc);
-        }
-        sk[4] = -tau * G * Wk;
-    }
-    for (int k = 0; k < n; ++k) {
-        float* sk = S + 8 * k;
-        for (int jj = 0; jj < n; ++jj) {
-            float* sj = S + 8 * jj;
-            const float d = (sk[0] - sj[0]) + (sk[1] - sj[1]);
-            const float u = d * sj[2];
-            float g2;
-            const float ec = erfc_as26(fabsf(u), g2);
-            const float E = copysignf(1.0f - ec, u);
-            sj[6] = fmaf(sk[4], 1.0f + E, sj[6]);
-            const float du = sk[4] * sj[3] * kTwoOverSqrtPi * g2;
-            sk[5] = fmaf(du, sj[2], sk[5]);
-            sj[5] = fmaf(-du, sj[2], sj[5]);
-            sj[7] = fmaf(du, d, sj[7]);
-        }
-    }
-    const float inv2tau = 0.5f / tau;
-    for (int k = 0; k < n; ++k) {
-        const float* sk = S + 8 * k;
-        const float dqt = fmaf(sk[4], inv2tau, -0.5f * sk[3] * sk[6]);  // a/4 = m/2
-        const float db = sk[7] / (4.0f * sk[2]);
-        float gv[9];
-        float4 r0, r1, r2, r3;
-        load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
-        const Trace tr = trace_px(r0, r1, r2, r3, px, py);
-        const int64_t o = vb + li[k];
-        chain_to_camera(__ldg(a.ws.rec2 + 2 * o), __ldg(a.ws.rec2 + 2 * o + 1), tr, r3, invF, dqt, sk[5], db, gv);
-        float* gc = a.ws.gcam + kGcamStride * (vb + li[k]);
-        red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
-        red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
-        red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_backward_generic(Args a) {
-    __shared__ int s_slot;
-    for (;;) {
-        const int t = next_tile(a, 0, &s_slot);
-        if (t < 0) return;
-        backward_tile_generic(a, t);
-    }
-}
-
 // Camera-space accumulators -> world-space gradients of each view's scene
 // (M = R M_w + T, P = R P_w Rᵀ): dM_w = Rᵀ dM, dP_w = Rᵀ G R, and the camera
 // pose dL/dR = dM M_wᵀ + 2 G R P_w, dL/dT = dM summed over the view's
@@ -717,11 +588,11 @@ int backward_blocks_per_sm(int KM) {
         case 20: return blocks_per_sm(k_backward<20, 8, false>, 128, backward_smem_bytes<20, 8>());
         case 24: return blocks_per_sm(k_backward<24, 8, false>, 128, backward_smem_bytes<24, 8>());
         case 32: return blocks_per_sm(k_backward<32, 8, false>, 128, backward_smem_bytes<32, 8>());
-        default: return blocks_per_sm(k_backward_generic, 256, 0);
+        default: return 1;  // lists longer than 32: voge_generic.cu
     }
 }
 
-// Launch the backward tile kernel for register-list capacity KM (0 = generic).
+// Launch the backward tile kernel for register-list capacity KM (8..32).
 template <int KM>
 static cudaError_t launch_backward_pair(const char* name, const char* wname, int nblocks, bool w, int kinds,
                                         cudaStream_t s, const Args& a) {
@@ -756,7 +627,7 @@ cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, c
         case 20: return launch_backward_pair<20>("k_backward<20>", "k_backward<20,wide>", nblocks, w, kinds, s, a);
         case 24: return launch_backward_pair<24>("k_backward<24>", "k_backward<24,wide>", nblocks, w, kinds, s, a);
         case 32: return launch_backward_pair<32>("k_backward<32>", "k_backward<32,wide>", nblocks, w, kinds, s, a);
-        default: return launch_tiles(k_backward_generic, "k_backward_generic", nblocks, 256, 0, s, a);
+        default: return cudaErrorInvalidValue;  // lists longer than 32: launch_backward_generic
     }
 }
 

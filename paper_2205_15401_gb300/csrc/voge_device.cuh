@@ -333,6 +333,37 @@ __device__ __forceinline__ void row_masks(const float4& r0, const float4& r1, co
     }
 }
 
+// Camera-space gradient of one (pixel, kept Gaussian) pair: out[0..2] = dM,
+// out[3..8] = G (xx, xy, xz, yy, yz, zz) with entries of P treated as independent.
+// s0, s1: the pair's second record (camera-space P and centre ray).
+__device__ __forceinline__ void chain_to_camera(const float4& s0, const float4& s1, const Trace& t, const float4& r3,
+                                                float invF, float dqt, float dl, float db, float out[9]) {
+    const float ib = rcp_approx(t.b);
+    const float Mz = r3.y;
+    const float dlt = -Mz * t.num * ib;  // l - Mz
+    const float dx = t.du * invF, dy = t.dv * invF;
+    const float D0 = s1.z + dx, D1 = s1.w + dy;  // D = (D0, D1, 1)
+    // V = M - l D = -Mz D' - (l - Mz) D
+    const float V0 = fmaf(-Mz, dx, -dlt * D0), V1 = fmaf(-Mz, dy, -dlt * D1), V2 = -dlt;
+    const float Pxx = s0.x, Pxy = s0.y, Pxz = s0.z, Pyy = s0.w, Pyz = s1.x, Pzz = s1.y;
+    const float PV0 = fmaf(Pxx, V0, fmaf(Pxy, V1, Pxz * V2));
+    const float PV1 = fmaf(Pxy, V0, fmaf(Pyy, V1, Pyz * V2));
+    const float PV2 = fmaf(Pxz, V0, fmaf(Pyz, V1, Pzz * V2));
+    const float PD0 = fmaf(Pxx, D0, fmaf(Pxy, D1, Pxz));
+    const float PD1 = fmaf(Pxy, D0, fmaf(Pyy, D1, Pyz));
+    const float PD2 = fmaf(Pxz, D0, fmaf(Pyz, D1, Pzz));
+    const float q2 = 2.0f * dqt, lb = dl * ib, lh = 0.5f * lb;
+    out[0] = fmaf(q2, PV0, lb * PD0);
+    out[1] = fmaf(q2, PV1, lb * PD1);
+    out[2] = fmaf(q2, PV2, lb * PD2);
+    out[3] = fmaf(dqt, V0 * V0, fmaf(lb, V0 * D0, db * D0 * D0));
+    out[4] = fmaf(dqt, V0 * V1, fmaf(lh, fmaf(V0, D1, D0 * V1), db * D0 * D1));
+    out[5] = fmaf(dqt, V0 * V2, fmaf(lh, fmaf(V0, 1.0f, D0 * V2), db * D0));
+    out[6] = fmaf(dqt, V1 * V1, fmaf(lb, V1 * D1, db * D1 * D1));
+    out[7] = fmaf(dqt, V1 * V2, fmaf(lh, fmaf(V1, 1.0f, D1 * V2), db * D1));
+    out[8] = fmaf(dqt, V2 * V2, fmaf(lb, V2, db));
+}
+
 // Camera-space gradient sums per record: 12 floats = three 16-byte groups
 // (dM0 dM1 dM2 G0 | G1 G2 G3 G4 | G5 0 0 0), G = (xx, xy, xz, yy, yz, zz).
 constexpr int kGcamStride = 12;

@@ -690,140 +690,6 @@ __global__ void __launch_bounds__(32, KM <= 20 ? 24 : 16) k_fine(Args a, int ngr
     cp_async_wait<0>();
 }
 
-// ---------------------------------------------------------------------------
-// Generic path for list lengths above the register lists (L > 32): same tile
-// staging, the per-pixel list kept sorted in the workspace.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void render_tile_generic(const Args& a, int t) {
-    constexpr int NT = 256, TH = 16;
-    extern __shared__ float4 smem[];
-    float4* stage = smem;
-    int32_t* sgid = reinterpret_cast<int32_t*>(stage + 4 * NT);
-
-    const int v = view_of_tile(a.views, a.hdr->nviews, t);
-    const ViewDesc& vd = a.views[v];
-    const int lt = t - vd.tile_base;
-    const int tiles_x = vd.tiles_x;
-    const int tx = lt % tiles_x, ty = lt / tiles_x;
-    const int H = vd.H, W = vd.W;
-    const int tid = threadIdx.x;
-    const int j = tx * kTileW + (tid & 15);
-    const int i = ty * TH + (tid >> 4);
-    const bool valid = (i < H) && (j < W);
-    const float px = (float)j + 0.5f, py = (float)i + 0.5f;
-    const int64_t pix = (int64_t)i * W + j;
-    const int64_t vb = vd.rec_base;
-    const int L = vd.L;
-    const int64_t gpix = vd.pix_base + pix;
-    float* lk = a.ws.gkey + gpix * (int64_t)a.ws.gen_L * 8;
-    int32_t* li = a.ws.gid + gpix * (int64_t)a.ws.gen_L;
-    int n = 0;
-    unsigned traced = 0;  // candidates this pixel traced (Eq. 6)
-
-    const TileSrc src = tile_source<NT>(a, vd, t);
-    bool active = valid;
-    for (int base = 0; base < src.count; base += NT) {
-        const int nc = min(NT, src.count - base);
-        if (tid < nc) {
-            int32_t g;
-            if (src.mode != 2) g = a.ws.tile_gauss[src.start + base + tid];
-            else g = base + tid;
-            float4 r0, r1, r2, r3;
-            load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
-            if (src.filter_box) {
-                const int4 tb = a.ws.tbox[vb + g];
-                if (tx < tb.x || tx > tb.y || ty < tb.z || ty > tb.w) {
-                    r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    r2 = r1;
-                }
-            }
-            stage[tid] = r0;
-            stage[NT + tid] = r1;
-            stage[2 * NT + tid] = r2;
-            stage[3 * NT + tid] = r3;
-            sgid[tid] = g;
-        }
-        __syncthreads();
-        if (active) {
-            for (int q = 0; q < nc; ++q) {
-                const float4 r3 = stage[3 * NT + q];
-                const float kth = (n == L) ? lk[L - 1] : INFINITY;
-                if (src.mode == 1 && r3.w > kth) {
-                    active = false;
-                    break;
-                }
-                const float l = candidate_key(stage[q], stage[NT + q], stage[2 * NT + q], r3, px, py, vd.Qeta);
-                ++traced;
-                if (l > 0.0f) {
-                    const int32_t g = sgid[q];
-                    if (n < L || l < lk[L - 1] || (l == lk[L - 1] && g < li[L - 1])) {
-                        int p = (n < L) ? n : L - 1;
-                        while (p > 0 && (lk[p - 1] > l || (lk[p - 1] == l && li[p - 1] > g))) {
-                            lk[p] = lk[p - 1];
-                            li[p] = li[p - 1];
-                            --p;
-                        }
-                        lk[p] = l;
-                        li[p] = g;
-                        if (n < L) ++n;
-                    }
-                }
-            }
-        }
-        if (__syncthreads_and(!active)) break;
-    }
-    {
-        const unsigned w_traced = __reduce_add_sync(0xffffffffu, traced);
-        const unsigned w_entries = __reduce_add_sync(0xffffffffu, (unsigned)n);
-        const unsigned w_pairs = __reduce_add_sync(0xffffffffu, (unsigned)(n * n));
-        if ((tid & 31) == 0) {
-            atomicAdd(&a.hdr->traces, (unsigned long long)w_traced);
-            atomicAdd(&a.hdr->entries, (unsigned long long)w_entries);
-            atomicAdd(&a.hdr->pairs, (unsigned long long)w_pairs);
-        }
-    }
-    if (valid) {
-        // fine pass with both loops over the list in global memory (L1 resident)
-        float* lw = vd.weights ? vd.weights + pix * L : nullptr;
-        for (int k = 0; k < n; ++k) {
-            float4 r0, r1, r2, r3;
-            load_rec(a.ws.rec, vb + li[k], r0, r1, r2, r3);
-            const Entry ek = entry_px(r0, r1, r2, r3, px, py);
-            float A = 0.0f;
-            for (int jj = 0; jj < n; ++jj) {
-                load_rec(a.ws.rec, vb + li[jj], r0, r1, r2, r3);
-                const Entry ej = entry_px(r0, r1, r2, r3, px, py);
-                const float u = ((ek.hi - ej.hi) + (ek.lo - ej.lo)) * ej.r;
-                const float q = erfc_as28(fabsf(u));
-                const float m = 0.5f * ej.a;
-                const float sm = copysignf(m, u);
-                A = fmaf(-sm, q, A + (m + sm));
-            }
-            lk[L + k] = ex2_approx(-vd.tau * kLog2e * A) * ek.a;  // W_k
-        }
-        for (int k = 0; k < L; ++k) {
-            const bool real = k < n;
-            vd.index[pix * L + k] = real ? li[k] : -1;
-            if (lw) lw[k] = real ? lk[L + k] : 0.0f;
-        }
-        for (int c = 0; c < vd.C; ++c) {
-            float acc = 0.0f;
-            for (int k = 0; k < n; ++k) acc = fmaf(lk[L + k], __ldg(vd.attr + (int64_t)li[k] * vd.C + c), acc);
-            vd.image[pix * vd.C + c] = acc;
-        }
-    }
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) k_render_generic(Args a) {
-    __shared__ int s_slot;
-    for (;;) {
-        const int t = next_tile(a, 1, &s_slot);
-        if (t < 0) return;
-        render_tile_generic(a, t);
-    }
-}
-
 size_t render_smem_bytes(int KM, int fine) {
     (void)fine;  // the fused and the selection-only kernel share one layout
     switch (KM) {
@@ -832,7 +698,7 @@ size_t render_smem_bytes(int KM, int fine) {
         case 20: return FwdSmem<20, 16>::bytes;
         case 24: return FwdSmem<24, 8>::bytes;
         case 32: return FwdSmem<32, 8>::bytes;
-        default: return (size_t)256 * 64 + 256 * 4;  // generic: stage[4][256] float4 + sgid
+        default: return 0;  // lists longer than 32: voge_generic.cu
     }
 }
 
@@ -866,7 +732,7 @@ int render_blocks_per_sm(int KM, int fine) {
             case 20: return blocks_per_sm(k_render<20, 16, true>, 256, render_smem_bytes(20, 1));
             case 24: return blocks_per_sm(k_render<24, 8, true>, 128, render_smem_bytes(24, 1));
             case 32: return blocks_per_sm(k_render<32, 8, true>, 128, render_smem_bytes(32, 1));
-            default: return blocks_per_sm(k_render_generic, 256, render_smem_bytes(0, 1));
+            default: return 1;
         }
     }
     switch (KM) {
@@ -875,11 +741,11 @@ int render_blocks_per_sm(int KM, int fine) {
         case 20: return blocks_per_sm(k_render<20, 16, false>, 256, render_smem_bytes(20, 0));
         case 24: return blocks_per_sm(k_render<24, 8, false>, 128, render_smem_bytes(24, 0));
         case 32: return blocks_per_sm(k_render<32, 8, false>, 128, render_smem_bytes(32, 0));
-        default: return blocks_per_sm(k_render_generic, 256, render_smem_bytes(0, 1));
+        default: return 1;
     }
 }
 
-// Launch the forward tile kernel for register-list capacity KM (0 = generic):
+// Launch the forward tile kernel for register-list capacity KM (8..32):
 // `nblocks` persistent CTAs that take tiles of class a.cls from the header.
 // fine = 0 launches the selection-only form (index lists only).
 cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args& a, int fine) {
@@ -890,7 +756,7 @@ cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args&
             case 20: return launch_tiles(k_render<20, 16, true>, "k_render<20>", nblocks, 256, render_smem_bytes(20, 1), s, a);
             case 24: return launch_tiles(k_render<24, 8, true>, "k_render<24>", nblocks, 128, render_smem_bytes(24, 1), s, a);
             case 32: return launch_tiles(k_render<32, 8, true>, "k_render<32>", nblocks, 128, render_smem_bytes(32, 1), s, a);
-            default: return launch_tiles(k_render_generic, "k_render_generic", nblocks, 256, render_smem_bytes(0, 1), s, a);
+            default: return cudaErrorInvalidValue;  // lists longer than 32: launch_render_generic
         }
     }
     switch (KM) {
