@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=4.0, help="measured seconds of each serving run")
     ap.add_argument("--no-configs", action="store_true", help="skip the forward / fwd+bwd rows of the other workloads")
+    ap.add_argument("--split-forward", action="store_true",
+                    help="the step's forward as two kernels (selection, then the fine pass): for profiling the fine pass")
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-posefit", action="store_true")
     ap.add_argument("--no-converters", action="store_true")
@@ -661,7 +663,8 @@ def main():
     sc = scenes.fit_8x512(seed=args.seed + rank, N=W["N"], B=W["views"], side=W["side"], C=W["C"], K=W["K"])
     cams = scenes.cameras(sc, voge.voge_pose_to_RT)
     N, C = W["N"], W["C"]
-    r = voge.Renderer(cams, N, C, K=W["K"], tau=W["tau"], thresh=W["eta"], device=dev)
+    r = voge.Renderer(cams, N, C, K=W["K"], tau=W["tau"], thresh=W["eta"],
+                      flags=voge.VOGE_FLAG_SPLIT_FORWARD if args.split_forward else 0, device=dev)
     P = r.pixels
 
     # flat parameter / gradient / Adam buffers: [means 3N | inv_cov 6N | attr CN]

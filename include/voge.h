@@ -46,7 +46,10 @@ enum {
     VOGE_ERR_UNSUPPORTED = -4,/* a combination this build does not implement */
     VOGE_ERR_TIMEOUT = -5,    /* a bounded wait ran out (serving) */
     VOGE_ERR_ADMISSION = -6,  /* request larger than the server's memory budget */
-    VOGE_ERR_BUSY = -7        /* no free slot / queue full (serving) */
+    VOGE_ERR_BUSY = -7,       /* no free slot / queue full (serving) */
+    VOGE_ERR_CHECK = -8       /* checked builds only (libvoge_checked.so): a kernel caught an index
+                                 outside its array; the access was redirected to element 0 and the
+                                 outputs of the call are not valid */
 };
 
 /* One view.  R row-major; M_cam = R M_world + T (Sec. 3.3).  F, Ox, Oy in

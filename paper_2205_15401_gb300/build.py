@@ -3,6 +3,10 @@
 Each .cu under csrc/ is compiled to an object in parallel, then linked into
 paper_2205_15401_gb300/libvoge.so against the shared CUDA runtime (the same
 libcudart.so.13 that PyTorch loads).  Objects go to paper_2205_15401_gb300/_build/.
+
+build(checked=True) makes the checked library, libvoge_checked.so (objects in
+_build_checked/), compiled with -DVOGE_CHECKED: the tile kernels check every
+gather and scatter index and the C ABI returns VOGE_ERR_CHECK when one fails.
 """
 from __future__ import annotations
 
@@ -19,6 +23,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvoge.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libvoge_checked.so")
+CHECKED_FLAGS = ["-DVOGE_CHECKED"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
               "--expt-relaxed-constexpr"]
@@ -39,27 +46,29 @@ def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-def _stamp():
+def _stamp(flags):
     h = hashlib.sha256()
     for f in _sources() + _headers():
         h.update(f.encode())
         h.update(open(f, "rb").read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(flags).encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile (if stale) and return the path of libvoge.so."""
-    stamp = _stamp()
-    stamp_file = os.path.join(BUILD, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=None, checked: bool = False) -> str:
+    """Compile (if stale) and return the path of libvoge.so, or of
+    libvoge_checked.so with checked=True."""
+    lib_path, build_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    flags = ARCH + NVCC_FLAGS + (CHECKED_FLAGS if checked else []) + list(extra_flags or [])
+    stamp = _stamp(flags)
+    stamp_file = os.path.join(build_dir, "stamp")
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = ARCH + NVCC_FLAGS + list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -71,16 +80,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
         ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

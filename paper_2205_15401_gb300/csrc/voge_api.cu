@@ -230,6 +230,21 @@ Args make_args(const Layout& l, void* ws) {
     return a;
 }
 
+#ifdef VOGE_CHECKED
+// Checked builds: wait for the call's kernels and report a failed index check
+// (the first failing site is in the call header).
+int finish_call(const Args& a, cudaStream_t s, int rc) {
+    if (rc != VOGE_OK) return rc;
+    int32_t site = 0;
+    if (cudaMemcpyAsync(&site, &a.hdr->check_site, sizeof(site), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return VOGE_ERR_CUDA;
+    return site ? VOGE_ERR_CHECK : VOGE_OK;
+}
+#else
+inline int finish_call(const Args&, cudaStream_t, int rc) { return rc; }
+#endif
+
 int record_grid(int64_t records) {
     int64_t g = (records + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -365,6 +380,7 @@ const char* voge_strerror(int code) {
         case VOGE_ERR_TIMEOUT: return "bounded wait ran out";
         case VOGE_ERR_ADMISSION: return "request exceeds the memory budget";
         case VOGE_ERR_BUSY: return "no free slot";
+        case VOGE_ERR_CHECK: return "checked build: a kernel caught an out-of-range index";
         default: return "unknown error";
     }
 }
@@ -403,12 +419,16 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
     int rc = upload_and_project(cams, p, l, a, b, 1, 1, s);
     if (rc != VOGE_OK) return rc;
     if (l.total_tiles == 0) return VOGE_OK;
-    if (l.KM == 0) return launch_render_generic(l.pixels, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
-    if (!split)
-        return launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a, 1) == cudaSuccess ? VOGE_OK
-                                                                                                     : VOGE_ERR_CUDA;
-    if (launch_render_tiles(l.KM, tile_grid(l.KM, 2, l.total_tiles), s, a, 0) != cudaSuccess) return VOGE_ERR_CUDA;
-    return launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+    cudaError_t e;
+    if (l.KM == 0) {
+        e = launch_render_generic(l.pixels, s, a);
+    } else if (!split) {
+        e = launch_render_tiles(l.KM, tile_grid(l.KM, 1, l.total_tiles), s, a, 1);
+    } else {
+        e = launch_render_tiles(l.KM, tile_grid(l.KM, 2, l.total_tiles), s, a, 0);
+        if (e == cudaSuccess) e = launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a);
+    }
+    return finish_call(a, s, e == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA);
 }
 
 int voge_render_fine(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
@@ -439,7 +459,8 @@ int voge_render_fine(const voge_camera* cams, const voge_params* p, const float*
     b.index_in = index;
     int rc = upload_and_project(cams, p, l, a, b, 1, 0, s);
     if (rc != VOGE_OK) return rc;
-    return launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a) == cudaSuccess ? VOGE_OK : VOGE_ERR_CUDA;
+    return finish_call(a, s, launch_fine(l.KM, l.total_tiles, l.TH, l.L, index, s, a) == cudaSuccess ? VOGE_OK
+                                                                                                   : VOGE_ERR_CUDA);
 }
 
 int voge_render_bwd(const voge_camera* cams, const voge_params* p, const float* means, const float* inv_cov,
@@ -491,7 +512,7 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
     if ((grad_means || grad_inv_cov || grad_cam || grad_attr) &&
         launch_grad_finalize(record_grid(p->N), p->B, p->N, 1, s, a) != cudaSuccess)
         return VOGE_ERR_CUDA;
-    return VOGE_OK;
+    return finish_call(a, s, VOGE_OK);
 }
 
 int voge_render_stats(const void* workspace, voge_render_stats_t* out, voge_stream_t stream_) {

@@ -85,7 +85,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
         for (int rw = 0; rw < 2; ++rw) {
             const int irow = row0 + 2 * warp + rw;
             const int cnt = irow < H ? ncols * L : 0;
-            const int32_t* src = vd.index_in + ((int64_t)irow * W + tx * kTileW) * L;
+            int64_t o0 = ((int64_t)irow * W + tx * kTileW) * L;
+            if (cnt > 0) o0 = VOGE_IDX(a.hdr, o0 + cnt - 1, (int64_t)H * W * L, kChkListRead) - (cnt - 1);
+            const int32_t* src = vd.index_in + o0;
             for (int x = lane; x < 16 * L; x += 32) *stg(rw * 16 * L + x) = x < cnt ? __ldg(src + x) : -1;
         }
     }
@@ -151,7 +153,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                 pp[h] = pixel_of(i);
                 kk[h] = i - __shfl_sync(0xffffffffu, excl, pp[h]);
                 px2[h] = (int64_t)(row0 + 2 * warp + (pp[h] >> 4)) * W + tx * kTileW + (pp[h] & 15);
-                gg[h] = __ldg(vd.index_in + px2[h] * L + kk[h]);
+                gg[h] = (int32_t)VOGE_IDX(
+                    a.hdr, __ldg(vd.index_in + VOGE_IDX(a.hdr, px2[h] * L + kk[h], (int64_t)H * W * L, kChkListRead)), N,
+                    kChkRecord);
             }
             float4 r[2][4];
             float c[2][3], gq[2][3], wk[2];
@@ -373,7 +377,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     for (int e0 = 0; e0 < n; e0 += 2) {
         int64_t o[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) o[h] = vb + __ldg(li + min(e0 + h, n - 1));
+        for (int h = 0; h < 2; ++h) o[h] = vb + VOGE_IDX(a.hdr, __ldg(li + min(e0 + h, n - 1)), N, kChkRecord);
         float4 r[2][4], q[2][2];
         float wk[2];
 #pragma unroll

@@ -102,9 +102,48 @@ struct BatchHdr {
     // what the forward pass of this call did (voge_render_stats): Gaussian-ray
     // traces of the coarse pass (Eq. 6 evaluations), kept entries, and the
     // fine pass's (k, j) pairs (sum over pixels of n_p^2)
-    unsigned long long traces, entries, pairs, pad2;
+    unsigned long long traces, entries, pairs;
+    int32_t check_site;     // checked builds: the first index check that failed (0: none)
+    int32_t pad3;
 };
 static_assert(sizeof(BatchHdr) % 16 == 0, "BatchHdr layout");
+
+// ------------------------------------------------------------------------
+// Checked builds (-DVOGE_CHECKED, build.py's checked library): every gather
+// and scatter index of the tile kernels goes through VOGE_IDX.  An index
+// outside [0, n) records its site in *site (the first one wins) and is
+// replaced by 0, a valid element, so the kernel reads or writes in bounds,
+// finishes, and the C ABI reports VOGE_ERR_CHECK.  Normal builds compile the
+// checks away.
+// ------------------------------------------------------------------------
+enum : int32_t {
+    kChkTileList = 1,  // candidate list of a tile (tile_gauss)
+    kChkRecord = 2,    // Gaussian index into records, attributes, gradients
+    kChkTile = 3,      // tile index (counts, offsets, boxes)
+    kChkListRead = 4,  // a pixel's index / weight list read back
+    kChkOutput = 5,    // image, weight or index output element
+    kChkScratch = 6,   // per-pixel scratch of the generic path
+    kChkBin = 7        // binning cursor
+};
+
+__host__ __device__ __forceinline__ bool in_bounds(int64_t i, int64_t n) { return (uint64_t)i < (uint64_t)n; }
+
+// i if 0 <= i < n, else 0 with the site recorded (first failure kept).
+__host__ __device__ __forceinline__ int64_t checked_index(int32_t* site, int64_t i, int64_t n, int32_t where) {
+    if (in_bounds(i, n)) return i;
+#ifdef __CUDA_ARCH__
+    atomicCAS(site, 0, where);
+#else
+    if (*site == 0) *site = where;
+#endif
+    return 0;
+}
+
+#ifdef VOGE_CHECKED
+#define VOGE_IDX(hdr, i, n, where) ::voge::checked_index(&(hdr)->check_site, (int64_t)(i), (int64_t)(n), (where))
+#else
+#define VOGE_IDX(hdr, i, n, where) (i)
+#endif
 
 // Projected record of one (view, Gaussian): 4 x float4 = 64 bytes.
 //   r0 = (uc_hi, uc_lo, vc_hi, vc_lo)   centre, pixel units (u = column + 0.5)

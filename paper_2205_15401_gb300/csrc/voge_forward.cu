@@ -49,8 +49,9 @@ __device__ __forceinline__ TileSrc tile_source(const Args& a, const ViewDesc& vd
         src.start = 0;
         return src;
     }
-    const int cnt = a.ws.tile_cnt[t];
-    const int off = a.ws.tile_off[t];
+    const int tc = (int)VOGE_IDX(a.hdr, t, a.hdr->total_tiles, kChkTile);
+    const int cnt = a.ws.tile_cnt[tc];
+    const int off = a.ws.tile_off[tc];
     if ((int64_t)off + cnt > a.ws.bin_cap) {  // binning overflowed: test every Gaussian against its box
         src.mode = 2;
         src.filter_box = 1;
@@ -124,7 +125,8 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
     const float py = (float)irow + 0.5f;
     const bool px_ok = lane < ncols;  // lanes 0..15 are the segment's pixels
     float* dw = vd.weights ? vd.weights + ((int64_t)irow * W + col0) * L : nullptr;
-    float* img = vd.image + ((int64_t)irow * W + col0) * C;
+    float* img = vd.image + (VOGE_IDX(a.hdr, ((int64_t)irow * W + col0 + ncols) * C - 1, (int64_t)H * W * C, kChkOutput) -
+                             ((int64_t)ncols * C - 1));
 
     // entry numbering: pixel p's entries are [pbase[p], pbase[p] + n_p)
     const int n = (lane < 16 && px_ok) ? np_lane : 0;
@@ -166,7 +168,8 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         for (int h = 0; h < 2; ++h) {
             const int i = min(i0 + 32 * h + lane, total - 1);
             pp[h] = pixel_of(i);
-            load_rec(a.ws.rec, vb + id_of(pp[h], i - pbase[pp[h]]), r[h][0], r[h][1], r[h][2], r[h][3]);
+            const int64_t g = VOGE_IDX(a.hdr, id_of(pp[h], i - pbase[pp[h]]), vd.N, kChkRecord);
+            load_rec(a.ws.rec, vb + g, r[h][0], r[h][1], r[h][2], r[h][3]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -216,7 +219,8 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         for (int k = n; k < L; ++k) Wst[lane * L + k] = 0.0f;
     __syncwarp();
     if (dw)  // [16][L] is the segment's layout: one coalesced copy
-        for (int x = lane; x < ncols * L; x += 32) dw[x] = Wst[x];
+        for (int x = lane; x < ncols * L; x += 32)
+            vd.weights[VOGE_IDX(a.hdr, ((int64_t)irow * W + col0) * L + x, (int64_t)H * W * L, kChkOutput)] = Wst[x];
     if (narrow) {
         // image: each pixel's lane adds W_k c_k over its list, eight rows in flight
         if (px_ok && lane < 16) {
@@ -228,7 +232,7 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
                 for (int u = 0; u < 8; ++u) {
                     const int k = min(k0 + u, n - 1);
                     w[u] = k0 + u < n ? Wst[lane * L + k] : 0.0f;
-                    const float* ap = vd.attr + (int64_t)id_of(lane, k) * C;
+                    const float* ap = vd.attr + VOGE_IDX(a.hdr, id_of(lane, k), vd.N, kChkRecord) * C;
                     c[u].x = __ldg(ap);
                     c[u].y = C > 1 ? __ldg(ap + 1) : 0.0f;
                     c[u].z = C > 2 ? __ldg(ap + 2) : 0.0f;
@@ -273,7 +277,7 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
                     const int kk = k0 + u * G + grp;
                     const int k = min(kk, np - 1);
                     w[u] = (on && kk < np) ? Wst[p * L + k] : 0.0f;
-                    const float* ap = vd.attr + (int64_t)id_of(p, k) * C;
+                    const float* ap = vd.attr + VOGE_IDX(a.hdr, id_of(p, k), vd.N, kChkRecord) * C;
                     if (!on) x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                     else if (v4) x[u] = __ldg(reinterpret_cast<const float4*>(ap) + cu);
                     else x[u] = make_float4(__ldg(ap + cu), 0.f, 0.f, 0.f);
@@ -382,8 +386,9 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
         const int nc = min(NT, src.count - base);
         if (tid < nc) {
             int32_t g;
-            if (src.mode != 2) g = a.ws.tile_gauss[src.start + base + tid];
+            if (src.mode != 2) g = a.ws.tile_gauss[VOGE_IDX(a.hdr, src.start + base + tid, a.ws.bin_cap, kChkTileList)];
             else g = base + tid;
+            g = (int32_t)VOGE_IDX(a.hdr, g, vd.N, kChkRecord);
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
             bool outside = false;
@@ -493,7 +498,9 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             // order) starts beyond its K-th depth can stop for good
             if (active && src.mode == 1 && nc == NT && base + NT < src.count) {
                 // the first candidate of the next chunk bounds everything after it
-                const int32_t gn = __ldg(a.ws.tile_gauss + src.start + base + NT);
+                const int32_t gn = (int32_t)VOGE_IDX(
+                    a.hdr, __ldg(a.ws.tile_gauss + VOGE_IDX(a.hdr, src.start + base + NT, a.ws.bin_cap, kChkTileList)), vd.N,
+                    kChkRecord);
                 const float nxt = __ldg(&a.ws.rec[4 * (vb + gn) + 3].w);
                 if (nxt > kbar) active = false;
             }
@@ -530,8 +537,9 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             for (int k = 0; k < L; ++k) istg[lane * L + k] = k < np_lane ? sli[k * NT + colb + lane] : -1;
         __syncwarp();
         if (irow < H) {
-            int32_t* di = vd.index + ((int64_t)irow * W + tx * kTileW) * L;
-            for (int x = lane; x < ncols * L; x += 32) di[x] = istg[x];
+            const int64_t o0 = ((int64_t)irow * W + tx * kTileW) * L;
+            for (int x = lane; x < ncols * L; x += 32)
+                vd.index[VOGE_IDX(a.hdr, o0 + x, (int64_t)H * W * L, kChkOutput)] = istg[x];
         }
         __syncwarp();
         if constexpr (FINE) {
@@ -609,7 +617,9 @@ __device__ __forceinline__ void fine_prefetch(const Args& a, int g, int r, int n
         const ViewDesc& vd = a.views[f.v];
         const int L = vd.L, W = vd.W;
         const int cnt = f.irow < vd.H ? min(kTileW, W - f.tx * kTileW) * L : 0;
-        const int32_t* src = vd.index_in + ((int64_t)f.irow * W + f.tx * kTileW) * L;
+        int64_t o0 = ((int64_t)f.irow * W + f.tx * kTileW) * L;
+        if (cnt > 0) o0 = VOGE_IDX(a.hdr, o0 + cnt - 1, (int64_t)vd.H * W * L, kChkListRead) - (cnt - 1);
+        const int32_t* src = vd.index_in + o0;
         if (v16) {
             for (int x = 4 * lane; x < cnt; x += 128) cp_async16(buf + x, src + x);
         } else {

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a, int64_t total_pi
     const int64_t vb = vd.rec_base;
     const float px = (float)q.j + 0.5f, py = (float)q.i + 0.5f;
     float* S = scratch_of(a, vd, pix);
+    if (VOGE_IDX(a.hdr, L, (int64_t)a.ws.gen_L + 1, kChkScratch) != L) return;  // scratch laid out for shorter lists
 
     // candidate source of the pixel's tile
     int mode, count, start = 0, filter_box = 0;
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a, int64_t total_pi
         mode = 2;
         count = N;
     } else {
-        const int cnt = a.ws.tile_cnt[q.tile], off = a.ws.tile_off[q.tile];
+        const int tc = (int)VOGE_IDX(a.hdr, q.tile, a.hdr->total_tiles, kChkTile);
+        const int cnt = a.ws.tile_cnt[tc], off = a.ws.tile_off[tc];
         if ((int64_t)off + cnt > a.ws.bin_cap) {
             mode = 2;
             count = N;
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a, int64_t total_pi
         int32_t g = -1;
         float lmin = INFINITY;
         if (qi < count) {
-            g = mode == 2 ? qi : a.ws.tile_gauss[start + qi];
+            g = mode == 2 ? qi : a.ws.tile_gauss[VOGE_IDX(a.hdr, start + qi, a.ws.bin_cap, kChkTileList)];
+            g = (int32_t)VOGE_IDX(a.hdr, g, N, kChkRecord);
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
             lmin = r3.w;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a, int64_t total_pi
     // entries
     for (int k = lane; k < n; k += 32) {
         float4 r0, r1, r2, r3;
-        load_rec(a.ws.rec, vb + __float_as_int(LS[8 * k + 1]), r0, r1, r2, r3);
+        load_rec(a.ws.rec, vb + VOGE_IDX(a.hdr, __float_as_int(LS[8 * k + 1]), N, kChkRecord), r0, r1, r2, r3);
         const Entry en = entry_px(r0, r1, r2, r3, px, py);
         *reinterpret_cast<float4*>(S + 8 * k + 4) = make_float4(en.hi, en.lo, en.r, 0.5f * en.a);
     }
@@ -254,8 +257,9 @@ __global__ void __launch_bounds__(256) k_render_generic(Args a, int64_t total_pi
     // outputs: index and weights in list order (padded), image = sum_k W_k c_k
     for (int k = lane; k < L; k += 32) {
         const bool in = k < n;
-        vd.index[pix * L + k] = in ? __float_as_int(LS[8 * k + 1]) : -1;
-        if (vd.weights) vd.weights[pix * L + k] = in ? WS[8 * k] : 0.0f;
+        const int64_t o = VOGE_IDX(a.hdr, pix * L + k, (int64_t)vd.H * W * L, kChkOutput);
+        vd.index[o] = in ? __float_as_int(LS[8 * k + 1]) : -1;
+        if (vd.weights) vd.weights[o] = in ? WS[8 * k] : 0.0f;
     }
     float* img = vd.image + pix * C;
     if (C <= 32) {
@@ -299,6 +303,7 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a, int64_t total_
     const float tau = vd.tau, invF = vd.invF;
     float* S = scratch_of(a, vd, pix);
     const int32_t* li = vd.index_in + pix * L;
+    if (VOGE_IDX(a.hdr, L, (int64_t)a.ws.gen_L + 1, kChkScratch) != L) return;  // scratch laid out for shorter lists
 
     // the list: entries before the first one outside [0, N)
     int n = L;
@@ -314,7 +319,7 @@ __global__ void __launch_bounds__(256) k_backward_generic(Args a, int64_t total_
     if (n == 0) return;
     for (int k = lane; k < n; k += 32) {
         float4 r0, r1, r2, r3;
-        load_rec(a.ws.rec, vb + __ldg(li + k), r0, r1, r2, r3);
+        load_rec(a.ws.rec, vb + VOGE_IDX(a.hdr, __ldg(li + k), N, kChkRecord), r0, r1, r2, r3);
         const Entry en = entry_px(r0, r1, r2, r3, px, py);
         *reinterpret_cast<float4*>(S + 8 * k) = make_float4(en.hi, en.lo, en.r, 0.5f * en.a);
         *reinterpret_cast<float4*>(S + 8 * k + 4) = make_float4(0.f, 0.f, 0.f, 0.f);

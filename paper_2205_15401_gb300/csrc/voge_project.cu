@@ -158,7 +158,8 @@ __device__ __forceinline__ void project_one(const Args& a, int v, int64_t t, int
         const int sub = g & (kTileSub - 1);
         for (int ty = tb.z; ty <= tb.w; ++ty)
             for (int tx = tb.x; tx <= tb.y; ++tx)
-                atomicAdd(&a.ws.tile_sub[(tile_base + ty * tiles_x + tx) * kTileSub + sub], 1);
+                atomicAdd(&a.ws.tile_sub[VOGE_IDX(a.hdr, tile_base + ty * tiles_x + tx, a.hdr->total_tiles, kChkTile) * kTileSub +
+                                         sub], 1);
     }
 }
 
@@ -257,9 +258,9 @@ __global__ void __launch_bounds__(256) k_scatter(Args a) {
         const int sub = g & (kTileSub - 1);
         for (int ty = tb.z; ty <= tb.w; ++ty)
             for (int tx = tb.x; tx <= tb.y; ++tx) {
-                const int tile = tile_base + ty * tiles_x + tx;
+                const int tile = (int)VOGE_IDX(a.hdr, tile_base + ty * tiles_x + tx, a.hdr->total_tiles, kChkTile);
                 const int pos = __ldg(a.ws.tile_off + tile) + atomicAdd(&a.ws.tile_sub[tile * kTileSub + sub], 1);
-                if (pos < a.ws.bin_cap) a.ws.tile_gauss[pos] = g;
+                if (pos < a.ws.bin_cap) a.ws.tile_gauss[VOGE_IDX(a.hdr, pos, a.ws.bin_cap, kChkBin)] = g;
             }
     }
 }
@@ -291,7 +292,7 @@ __device__ __forceinline__ uint32_t keep(uint32_t mine, uint32_t other, bool tak
 
 template <int E>
 __device__ __forceinline__ void sort_tile_block(const Args& a, uint32_t* sw, int32_t* sg, int cnt, int off, int n2,
-                                                int64_t vb) {
+                                                int64_t vb, int vd_N) {
     const int tid = threadIdx.x;
     const int nthr = n2 / E;  // threads holding entries (a multiple of 32 or all of n2 < 32)
     const bool act = tid < nthr;
@@ -301,7 +302,8 @@ __device__ __forceinline__ void sort_tile_block(const Args& a, uint32_t* sw, int
         const int x = tid * E + r;
         w[r] = ~0u;
         if (act && x < cnt) {
-            const int32_t g = a.ws.tile_gauss[off + x];
+            const int32_t g = (int32_t)VOGE_IDX(a.hdr, a.ws.tile_gauss[VOGE_IDX(a.hdr, off + x, a.ws.bin_cap, kChkTileList)],
+                                                vd_N, kChkRecord);
             sg[x] = g;
             w[r] = (float_order(__ldg(&a.ws.rec[4 * (vb + g) + 3].w)) & ~((1u << kSortPosBits) - 1u)) | (uint32_t)x;
         }
@@ -366,10 +368,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Args a) {
         int n2 = 2;
         while (n2 < cnt) n2 <<= 1;
         const int64_t vb = vd.rec_base;
-        if (n2 <= 256) sort_tile_block<1>(a, sw, sg, cnt, off, n2, vb);
-        else if (n2 == 512) sort_tile_block<2>(a, sw, sg, cnt, off, n2, vb);
-        else if (n2 == 1024) sort_tile_block<4>(a, sw, sg, cnt, off, n2, vb);
-        else sort_tile_block<8>(a, sw, sg, cnt, off, n2, vb);
+        if (n2 <= 256) sort_tile_block<1>(a, sw, sg, cnt, off, n2, vb, vd.N);
+        else if (n2 == 512) sort_tile_block<2>(a, sw, sg, cnt, off, n2, vb, vd.N);
+        else if (n2 == 1024) sort_tile_block<4>(a, sw, sg, cnt, off, n2, vb, vd.N);
+        else sort_tile_block<8>(a, sw, sg, cnt, off, n2, vb, vd.N);
         __syncthreads();  // the next tile reuses sw and sg
     }
 }

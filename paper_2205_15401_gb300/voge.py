@@ -13,6 +13,7 @@ per-pixel index lists and weights).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -22,8 +23,10 @@ import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvoge.so")
+CHECKED_LIB_PATH = os.path.join(_PKG, "libvoge_checked.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_use_checked = False
 
 VOGE_OK = 0
 VOGE_FLAG_PLAIN = 1
@@ -57,13 +60,14 @@ class voge_params(ctypes.Structure):
 
 
 def lib():
-    """Load libvoge.so (built in-tree); raises if it is missing."""
-    global _lib
+    """Load libvoge.so (built in-tree), or libvoge_checked.so inside
+    checked_library(); raises if it is missing."""
+    path = CHECKED_LIB_PATH if _use_checked else LIB_PATH
     with _lock:
-        if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_15401_gb300.build.build()")
-            L = ctypes.CDLL(LIB_PATH)
+        if path not in _libs:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with paper_2205_15401_gb300.build.build()")
+            L = ctypes.CDLL(path)
             vp, P = ctypes.c_void_p, ctypes.POINTER
             L.voge_version.restype = ctypes.c_int
             L.voge_strerror.restype = ctypes.c_char_p
@@ -113,8 +117,22 @@ def lib():
             L.voge_trace_reset.restype = None
             L.voge_measure_alu_peaks.argtypes = [P(voge_alu_peaks), vp]
             L.voge_measure_alu_peaks.restype = ctypes.c_int
-            _lib = L
-    return _lib
+            _libs[path] = L
+    return _libs[path]
+
+
+@contextlib.contextmanager
+def checked_library():
+    """Within the block every binding call goes to libvoge_checked.so (built by
+    build.build(checked=True)): the tile kernels check their gather and
+    scatter indices, and a failed check raises (VOGE_ERR_CHECK)."""
+    global _use_checked
+    prev = _use_checked
+    _use_checked = True
+    try:
+        yield
+    finally:
+        _use_checked = prev
 
 
 def _check(rc, what):

@@ -54,7 +54,7 @@ def test_library_is_built_for_sm103a():
 def test_version_and_errors(voge):
     assert voge.voge_version() >= 100
     L = voge.lib()
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert len(L.voge_strerror(code)) > 0
 
 
