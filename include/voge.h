@@ -87,7 +87,10 @@ enum {
     VOGE_FLAG_PLAIN = 1,
     /* voge_render_bwd only: reuse the projection that the matching
      * voge_render_fwd call left in the same workspace (same cams, params and
-     * Gaussians, workspace untouched in between) instead of recomputing it. */
+     * Gaussians, workspace untouched in between) instead of recomputing it.
+     * When index is that call's index output (the same buffer, unchanged),
+     * its record of which 16 x 2-pixel row pairs kept an entry is reused
+     * too, so that the backward skips the others without reading them. */
     VOGE_FLAG_REUSE_PROJECTION = 2,
     /* voge_render_fwd only: run the coarse pass (selection) and the fine pass
      * as two kernels -- the selection writes the index lists, then the fine

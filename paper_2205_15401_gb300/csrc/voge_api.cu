@@ -17,7 +17,7 @@ cudaError_t launch_render_tiles(int KM, int nblocks, cudaStream_t s, const Args&
 cudaError_t launch_fine(int KM, int total_tiles, int tile_h, int L, const void* index, cudaStream_t s,
                         const Args& a);
 cudaError_t launch_backward_tiles(int KM, int nblocks, int with_wk, int kinds, cudaStream_t s, const Args& a);
-cudaError_t launch_backward_packed(int KM, int nblocks, cudaStream_t s, const Args& a);
+cudaError_t launch_backward_packed(int KM, int nblocks, int live_tiles, cudaStream_t s, const Args& a);
 cudaError_t launch_grad_finalize(int grid, int nviews, int N, int shared_scene, cudaStream_t s, const Args& a);
 int render_blocks_per_sm(int KM, int fine);
 cudaError_t launch_render_generic(int64_t total_pixels, cudaStream_t s, const Args& a);
@@ -74,7 +74,7 @@ void pick_variant(int L, int* KM, int* TH) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t desc, rec, rec2, tbox, tile_cnt, tile_off, tile_sub, tile_gauss, gcam, gkey, gid, total;
+    size_t desc, live_hdr, rec, rec2, tbox, tile_cnt, tile_off, tile_sub, tile_gauss, gcam, live, gkey, gid, total;
     int64_t pixels, bin_cap;
     int32_t total_tiles, TH, KM, L;
 };
@@ -112,7 +112,8 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.bin_cap = BN * cap;
     if (l.bin_cap > (int64_t)INT32_MAX) l.bin_cap = INT32_MAX;
     size_t o = 0;
-    l.desc = o; o = align256(o + sizeof(BatchHdr) + sizeof(ViewDesc) * p->B);
+    l.live_hdr = o + sizeof(BatchHdr) + sizeof(ViewDesc) * p->B;
+    l.desc = o; o = align256(o + sizeof(BatchHdr) + sizeof(ViewDesc) * p->B + sizeof(LiveHdr));
     l.rec = o; o = align256(o + 64 * (size_t)BN);
     l.rec2 = o; o = align256(o + 32 * (size_t)BN);
     l.tbox = o; o = align256(o + 16 * (size_t)BN);
@@ -121,6 +122,8 @@ Layout make_layout(const voge_camera* cams, const voge_params* p) {
     l.tile_sub = o; o = align256(o + 4 * (size_t)kTileSub * (size_t)(tiles + 1));
     l.tile_gauss = o; o = align256(o + 4 * (size_t)l.bin_cap);
     l.gcam = o; o = align256(o + 4 * kGcamStride * (size_t)BN);
+    // packed backward's live row pairs: at most 4 row pairs x 2 backward tiles per tile
+    l.live = o; o = align256(o + 8 * 8 * (size_t)(tiles + 1));
     if (l.KM == 0 && l.L > 0) {
         l.gkey = o; o = align256(o + 32 * (size_t)pixels * l.L);  // 8 floats per entry
         l.gid = o; o = align256(o + 4 * (size_t)pixels * l.L);
@@ -143,6 +146,8 @@ Ws make_ws(const Layout& l, void* base) {
     w.tile_gauss = reinterpret_cast<int32_t*>(b + l.tile_gauss);
     w.bin_cap = l.bin_cap;
     w.gcam = reinterpret_cast<float*>(b + l.gcam);
+    w.live = reinterpret_cast<int2*>(b + l.live);
+    w.live_hdr = reinterpret_cast<LiveHdr*>(b + l.live_hdr);
     w.gkey = reinterpret_cast<float*>(b + l.gkey);
     w.gid = reinterpret_cast<int32_t*>(b + l.gid);
     w.gen_L = l.L;
@@ -157,15 +162,18 @@ struct Buffers {
     const float* weights_in;
     const float* grad_image;
     float *grad_means, *grad_inv_cov, *grad_attr, *grad_cam;
+    const int32_t* live_for;  // the lists whose live row pairs this call records (null: none)
 };
 
 // View table of a render call: every view shares the scene; outputs are
 // laid out view after view.
 void build_views(const voge_camera* cams, const voge_params* p, const Layout& l, const Buffers& b,
                  std::vector<unsigned char>& blob) {
-    blob.assign(sizeof(BatchHdr) + sizeof(ViewDesc) * p->B, 0);
+    blob.assign(sizeof(BatchHdr) + sizeof(ViewDesc) * p->B + sizeof(LiveHdr), 0);
     BatchHdr* h = reinterpret_cast<BatchHdr*>(blob.data());
     ViewDesc* vd = reinterpret_cast<ViewDesc*>(blob.data() + sizeof(BatchHdr));
+    LiveHdr* lh = reinterpret_cast<LiveHdr*>(blob.data() + sizeof(BatchHdr) + sizeof(ViewDesc) * p->B);
+    lh->index_fwd = b.live_for;
     const int use_thresh = p->thresh > 0.0f ? 1 : 0;
     const float Qeta = use_thresh ? (p->thresh >= 1.0f ? 0.0f : (float)(2.0 * log(1.0 / (double)p->thresh))) : INFINITY;
     int32_t tile_base = 0;
@@ -257,7 +265,10 @@ int upload_and_project(const voge_camera* cams, const voge_params* p, const Layo
                        const Buffers& b, int project, int bin, cudaStream_t s) {
     std::vector<unsigned char> blob;
     build_views(cams, p, l, b, blob);
-    if (cudaMemcpyAsync(a.hdr, blob.data(), blob.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // a call that reuses the forward's projection keeps its record of live
+    // row pairs (the blob's tail) as well
+    const size_t bytes = blob.size() - (project ? 0 : sizeof(LiveHdr));
+    if (cudaMemcpyAsync(a.hdr, blob.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return VOGE_ERR_CUDA;
     if (!project) return VOGE_OK;
     const int count_tiles = bin && !(p->flags & VOGE_FLAG_PLAIN);
@@ -414,6 +425,7 @@ int voge_render_fwd(const voge_camera* cams, const voge_params* p, const float* 
     b.image = image;
     b.weights = weights;
     b.index = index;
+    if (l.KM > 0) b.live_for = index;  // the tile kernels record the row pairs that keep an entry
     const bool split = (p->flags & VOGE_FLAG_SPLIT_FORWARD) && l.KM != 0;
     if (split) b.index_in = index;  // the fine kernel reads the lists the selection kernel wrote
     int rc = upload_and_project(cams, p, l, a, b, 1, 1, s);
@@ -496,14 +508,19 @@ int voge_render_bwd_w(const voge_camera* cams, const voge_params* p, const float
     b.grad_attr = grad_attr;
     b.grad_cam = grad_cam;
     const int project = (p->flags & VOGE_FLAG_REUSE_PROJECTION) ? 0 : 1;
+    // the packed form works through the row pairs that keep an entry: from the
+    // forward's record when the projection (and so the record) is reused,
+    // else found here by k_live_units
+    const bool packed = weights && p->C <= 3 && l.KM > 0 && l.KM <= 20;
+    if (packed && project) b.live_for = index;
     int rc = upload_and_project(cams, p, l, a, b, project, 0, s);
     if (rc != VOGE_OK) return rc;
     if (cudaMemsetAsync(a.ws.gcam, 0, 4 * kGcamStride * (size_t)p->B * p->N, s) != cudaSuccess) return VOGE_ERR_CUDA;
     if (l.total_tiles > 0) {
-        const bool packed = weights && p->C <= 3 && l.KM > 0 && l.KM <= 20;
         const cudaError_t e =
             l.KM == 0 ? launch_backward_generic(l.pixels, s, a)
-            : packed  ? launch_backward_packed(l.KM, tile_grid(l.KM, 0, l.total_tiles), s, a)
+            : packed  ? launch_backward_packed(l.KM, tile_grid(l.KM, 0, 2 * l.total_tiles), project ? l.total_tiles : 0,
+                                               s, a)
                       : launch_backward_tiles(l.KM, tile_grid(l.KM, 0, l.total_tiles), weights ? 0 : 1,
                                               p->C >= 8 ? 2 : 1, s, a);
         if (e != cudaSuccess) return VOGE_ERR_CUDA;

@@ -23,6 +23,18 @@ namespace voge {
 
 constexpr float kTwoOverSqrtPi = 1.1283791670955126f;
 
+// Entries per step of the chain rule's loop (their gathers are in flight
+// together; 4 measured faster than 2 or 3), and entries per lane per step of
+// the packed set-up (2 measured faster than 3 or 4).
+#ifndef VOGE_CHAIN_STEP
+#define VOGE_CHAIN_STEP 4
+#endif
+constexpr int kChainStep = VOGE_CHAIN_STEP;
+#ifndef VOGE_SETUP_STEP
+#define VOGE_SETUP_STEP 2
+#endif
+constexpr int kSetupStep = VOGE_SETUP_STEP;
+
 // How a tile adds the attribute gradient dL/dc_g += W_k dL/dI:
 //   kAttrLane:  one reduction per lane and channel (4 <= C < 8),
 //   kAttrWarp:  warp-cooperative rows, lanes over (source pixel, channel) (C >= 8),
@@ -42,17 +54,63 @@ constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3, kAttr
 template <int KM, int TH>
 __host__ __device__ constexpr bool wk_in_smem() { return KM <= 20; }
 
-// One backward tile: rows [hb TH, hb TH + TH) of binning tile t (the
-// backward reads the index lists, not the tile lists, so it may split the
-// forward's tiles into shorter ones).
-template <int KM, int TH, int AM>
-__device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
+// Packed backward: the calling warp's asynchronous copies of the index
+// lists of unit (t, hb, q) of view v, transposed on the way into its columns
+// of sid ([list position][pixel of the block]): word x of a row's [16][L]
+// block is list position x % L of column x / L (L <= 20 < 32, so one carry
+// per step).  Pixels outside the image are never read.  One commit group.
+template <int TH>
+__device__ __forceinline__ void stage_lists_packed(const Args& a, int32_t* sid, int v, int t, int hb, int q) {
+    constexpr int NT = 16 * TH;
+    const ViewDesc& vd = a.views[v];
+    const int lt = t - vd.tile_base;
+    const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
+    const int H = vd.H, W = vd.W, L = vd.L;
+    const int row0 = ty * vd.tile_h + hb * TH + 2 * q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncols = min(kTileW, W - tx * kTileW);
+    const int dc = 32 / L, dk = 32 - dc * L;
+#pragma unroll
+    for (int rw = 0; rw < 2; ++rw) {
+        const int irow = row0 + rw;
+        const int cnt = irow < H ? ncols * L : 0;
+        int64_t o0 = ((int64_t)irow * W + tx * kTileW) * L;
+        if (cnt > 0) o0 = VOGE_IDX(a.hdr, o0 + cnt - 1, (int64_t)H * W * L, kChkListRead) - (cnt - 1);
+        const int32_t* src = vd.index_in + o0;
+        int col = lane / L, k = lane - col * L;
+        int32_t* dst = sid + 32 * warp + 16 * rw;
+        for (int x = lane; x < cnt; x += 32) {
+            cp_async4(dst + k * NT + col, src + x);
+            k += dk;
+            col += dc;
+            if (k >= L) {
+                k -= L;
+                ++col;
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
+// Rows 2q and 2q + 1 of one backward tile, rows [hb TH, hb TH + TH) of
+// binning tile t of view v (v < 0: looked up) -- the backward reads the index
+// lists, not the tile lists, so it may split the forward's tiles into shorter
+// ones -- for the calling warp, in its warp's shared-memory columns.  The
+// packed form finds its lists already staged in sid (stage_lists_packed) and
+// calls next() once, as soon as sid is free again, so that the caller can
+// stage its next unit while this one runs.
+template <int KM, int TH, int AM, typename Hook = NoHook>
+__device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int q, int v = -1, Hook next = Hook()) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     float4* jst = smem;  // [KM][NT]
     float* swk = reinterpret_cast<float*>(jst + KM * NT);  // [KM][NT] W_k (kAttrChain)
 
-    const int v = view_of_tile(a.views, a.hdr->nviews, t);
+    if (v < 0) v = view_of_tile(a.views, a.hdr->nviews, t);
     const ViewDesc& vd = a.views[v];
     const int lt = t - vd.tile_base;
     const int tiles_x = vd.tiles_x;
@@ -60,9 +118,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     const int H = vd.H, W = vd.W;
     const float invF = vd.invF;
     const int tid = threadIdx.x;
-    const int row0 = ty * vd.tile_h + hb * TH;  // first pixel row of this backward tile
+    const int row0 = ty * vd.tile_h + hb * TH + 2 * q;  // first pixel row of this warp's pair
     const int j = tx * kTileW + (tid & 15);
-    const int i = row0 + (tid >> 4);
+    const int i = row0 + ((tid >> 4) & 1);
     const bool valid = (i < H) && (j < W);
     const float px = (float)j + 0.5f, py = (float)i + 0.5f;
     const int64_t pix = (int64_t)i * W + j;
@@ -72,18 +130,24 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     const float* attr = vd.attr;
     float* grad_attr = vd.grad_attr;
 
-    // index lists: each warp reads its two 16-pixel row segments (contiguous
-    // [16][L] blocks) with consecutive lanes on consecutive words, through its
-    // own shared-memory columns
+    constexpr bool packed = AM == kAttrPacked;
+    // staged index lists of the packed set-up, in the layout of the W_k
+    // buffer, which takes each entry's dA_k in place of its index once the
+    // entry is set up
+    int32_t* sid = reinterpret_cast<int32_t*>(swk);
     const int lane = tid & 31, warp = tid >> 5;
     auto stg = [&](int x) -> int32_t* {
         return reinterpret_cast<int32_t*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127);
     };
-    {
+    if constexpr (packed) {
+        cp_async_wait<0>();
+    } else {
+        // each warp reads its two 16-pixel row segments (contiguous [16][L]
+        // blocks) with consecutive lanes on consecutive words
         const int ncols = min(kTileW, W - tx * kTileW);
 #pragma unroll
         for (int rw = 0; rw < 2; ++rw) {
-            const int irow = row0 + 2 * warp + rw;
+            const int irow = row0 + rw;
             const int cnt = irow < H ? ncols * L : 0;
             int64_t o0 = ((int64_t)irow * W + tx * kTileW) * L;
             if (cnt > 0) o0 = VOGE_IDX(a.hdr, o0 + cnt - 1, (int64_t)H * W * L, kChkListRead) - (cnt - 1);
@@ -93,7 +157,13 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     }
     __syncwarp();
     // a warp whose 32 lists are all empty has nothing to add
-    if (!__any_sync(0xffffffffu, valid && *stg(lane * L) >= 0)) return;
+    if (!__any_sync(0xffffffffu, valid && (packed ? sid[tid] : *stg(lane * L)) >= 0)) {
+        if constexpr (packed) {
+            __syncwarp();  // every lane has read sid
+            next();
+        }
+        return;
+    }
     // Kept entries occupy slots [KM - K, KM - K + n); slot s holds list
     // position k = s - (KM - K).  The indices live in registers only while
     // the entries are set up; later stages reload them from the list (the
@@ -106,61 +176,79 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     constexpr bool kChain = AM == kAttrChain || AM == kAttrPacked;
     const bool early = wi != nullptr && C <= 3 && AM != kAttrWarp && AM != kAttrLane;
     float ga0 = 0.0f, ga1 = 0.0f, ga2 = 0.0f;
-    constexpr bool packed = AM == kAttrPacked;
     if constexpr (packed) {
         // Set-up with the entries packed over the lanes (the forward's W_k are
-        // supplied and C <= 3): entry i of the warp's 32 lists -- pixel p,
-        // list position k -- is set up by one lane, so that 32 entries'
-        // record, attribute, image-gradient and weight loads are in flight at
-        // once.  Its (l, r, m) go to the stream and dA_k to the W_k buffer
-        // (unused when W comes from the forward).
+        // supplied and C <= 3).  The warp's kept entries are enumerated by
+        // list position first: row k holds the pixels whose lists are longer
+        // than k (mask M_k, nested since lists are prefixes), so consecutive
+        // lanes take neighbouring pixels at one position -- distinct shared-
+        // memory banks, and often the same record.  Each entry's (l, r, m)
+        // goes to the stream and dA_k replaces its staged index.
         float* sdA = swk;
         {
             bool open = valid;
 #pragma unroll
             for (int s = 0; s < KM; ++s) {
                 if (s < K) {
-                    const int32_t g = *stg(lane * L + s);
+                    const int32_t g = sid[s * NT + tid];
                     open = open && g >= 0 && g < N;
                     n += open ? 1 : 0;
                 }
             }
         }
-        __syncwarp();  // the ids are read (the stream overwrites their staging rows)
-        int incl = n;
+        // lane k < KM holds M_k and the number of entries before row k
+        unsigned mrow = 0u;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, n > k);
+            if (lane == k) mrow = m;
+        }
+        const int cnt = __popc(mrow);
+        int incl = cnt;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += t;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - n;
-        auto pixel_of = [&](int i) -> int {  // the last lane p with excl_p <= i
-            int p = 0;
+        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cnt;
+        for (int i0 = 0; i0 < total; i0 += 32 * kSetupStep) {
+            int pp[kSetupStep], kk[kSetupStep];
+            int32_t gg[kSetupStep];
+            int64_t px2[kSetupStep];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int b = __shfl_sync(0xffffffffu, excl, p + step);
-                if (b <= i) p += step;
-            }
-            return p;
-        };
-        for (int i0 = 0; i0 < total; i0 += 64) {
-            int pp[2], kk[2];
-            int32_t gg[2];
-            int64_t px2[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kSetupStep; ++h) {
                 const int i = min(i0 + 32 * h + lane, total - 1);
-                pp[h] = pixel_of(i);
-                kk[h] = i - __shfl_sync(0xffffffffu, excl, pp[h]);
-                px2[h] = (int64_t)(row0 + 2 * warp + (pp[h] >> 4)) * W + tx * kTileW + (pp[h] & 15);
-                gg[h] = (int32_t)VOGE_IDX(
-                    a.hdr, __ldg(vd.index_in + VOGE_IDX(a.hdr, px2[h] * L + kk[h], (int64_t)H * W * L, kChkListRead)), N,
-                    kChkRecord);
-            }
-            float4 r[2][4];
-            float c[2][3], gq[2][3], wk[2];
+                int k = 0;  // the last row whose first entry is at or before i
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int b = __shfl_sync(0xffffffffu, excl, k + step);
+                    if (k + step < KM && b <= i) k += step;
+                }
+                // the (i - first)-th set bit of M_k, by halving popcounts
+                unsigned m = __shfl_sync(0xffffffffu, mrow, k);
+                int r = i - __shfl_sync(0xffffffffu, excl, k), p = 0;
+#pragma unroll
+                for (int w = 16; w >= 1; w >>= 1) {
+                    const int c = __popc(m & ((1u << w) - 1u));
+                    if (r >= c) {
+                        r -= c;
+                        m >>= w;
+                        p += w;
+                    }
+                }
+                pp[h] = p;
+                kk[h] = k;
+                px2[h] = (int64_t)(row0 + (p >> 4)) * W + tx * kTileW + (p & 15);
+                // a lane past the last entry reads no staged index (its owner
+                // may already have replaced it) and gathers record 0
+                gg[h] = i0 + 32 * h + lane < total
+                            ? (int32_t)VOGE_IDX(a.hdr, sid[k * NT + 32 * warp + p], N, kChkRecord)
+                            : 0;
+            }
+            float4 r[kSetupStep][4];
+            float c[kSetupStep][3], gq[kSetupStep][3], wk[kSetupStep];
+#pragma unroll
+            for (int h = 0; h < kSetupStep; ++h) {
                 load_rec(a.ws.rec, vb + gg[h], r[h][0], r[h][1], r[h][2], r[h][3]);
                 const float* ck = attr + (int64_t)gg[h] * C;
                 const float* gp0 = vd.grad_image + px2[h] * C;
@@ -173,11 +261,11 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                 wk[h] = __ldg(vd.weights_in + px2[h] * L + kk[h]);
             }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kSetupStep; ++h) {
                 if (i0 + 32 * h + lane < total) {
                     const int p = pp[h];
                     const float pxp = (float)(tx * kTileW + (p & 15)) + 0.5f;
-                    const float pyp = (float)(row0 + 2 * warp + (p >> 4)) + 0.5f;
+                    const float pyp = (float)(row0 + (p >> 4)) + 0.5f;
                     const Entry e = entry_px(r[h][0], r[h][1], r[h][2], r[h][3], pxp, pyp);
                     const float G = fmaf(gq[h][2], c[h][2], fmaf(gq[h][1], c[h][1], gq[h][0] * c[h][0]));
                     jst[kk[h] * NT + 32 * warp + p] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
@@ -201,6 +289,8 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
                 dA[s] = 0.0f;
             }
         }
+        __syncwarp();  // every lane has read its dA_k: sid is free
+        next();
     } else if (early && valid) {
         const float* gp0 = vd.grad_image + pix * C;
         ga0 = __ldg(gp0);
@@ -270,7 +360,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     const int spi = cw <= 32 ? 32 / cw : 1;  // source lanes per step
     const int sub = cw <= 32 ? lane / cw : 0;
     const int cc = cw <= 32 ? lane - sub * cw : lane;
-    const int64_t pbase = (int64_t)(row0 + 2 * warp) * W + tx * kTileW;
+    const int64_t pbase = (int64_t)(row0) * W + tx * kTileW;
     if (!early) {
         int e = 0;
 #pragma unroll
@@ -347,18 +437,27 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
             acc_s += du;
             acc_dr = fmaf(du, d, acc_dr);
         }
-        jst[e * NT + tid] = make_float4(acc_dm, -acc_s * J.z, acc_dr, 0.0f);
+        // j-side parts of dqt_j = dA_j / (2 tau) - a_j dm_j / 4 (a_j = 2 m_j)
+        // and of dl_j; db_j = dr_j / (4 r_j) in full
+        jst[e * NT + tid] = make_float4(-0.5f * J.w * acc_dm, -acc_s * J.z, acc_dr * rcp_approx(4.0f * J.z), 0.0f);
     }
-    // the chain rule reads each entry's results from the stream: .y gets the
-    // k-side sum dl, .w the k-side dA
+    // the chain rule reads each entry's (dqt, dl, db, index) from the stream:
+    // .x gets the k-side dA_k / (2 tau), .y the k-side dl, .w the index (all
+    // of the pixel's indices are loaded at once here, so that the chain's
+    // record gathers wait on shared memory only)
+    const float inv2tau = 0.5f / tau;
     {
+        int32_t gid[KM];
+#pragma unroll
+        for (int s = 0; s < KM; ++s) gid[s] = kept(s) ? __ldg(li + (s - (KM - K))) : 0;
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
             if (kept(s)) {
                 float4 J = jst[e * NT + tid];
+                J.x = fmaf(dA[s], inv2tau, J.x);
                 J.y += dl[s];
-                J.w = dA[s];
+                J.w = __int_as_float(gid[s]);
                 jst[e * NT + tid] = J;
                 ++e;
             }
@@ -366,22 +465,25 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
     }
     // chain rule to camera space: a run-time loop over the entries, so that
     // it holds no per-slot registers
-    const float inv2tau = 0.5f / tau;
     float gi0 = 0.0f, gi1 = 0.0f, gi2 = 0.0f;  // dL/dI of this pixel (kAttrChain)
     if (kChain) {
         gi0 = __ldg(gp);
         if (C > 1) gi1 = __ldg(gp + 1);
         if (C > 2) gi2 = __ldg(gp + 2);
     }
-    // two entries at a time: their ids, then both records and second records
-    for (int e0 = 0; e0 < n; e0 += 2) {
-        int64_t o[2];
+    // kChainStep entries at a time: their records and second records
+    for (int e0 = 0; e0 < n; e0 += kChainStep) {
+        float4 J[kChainStep];
+        int64_t o[kChainStep];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) o[h] = vb + VOGE_IDX(a.hdr, __ldg(li + min(e0 + h, n - 1)), N, kChkRecord);
-        float4 r[2][4], q[2][2];
-        float wk[2];
+        for (int h = 0; h < kChainStep; ++h) {
+            J[h] = jst[min(e0 + h, n - 1) * NT + tid];
+            o[h] = vb + VOGE_IDX(a.hdr, __float_as_int(J[h].w), N, kChkRecord);
+        }
+        float4 r[kChainStep][4], q[kChainStep][2];
+        float wk[kChainStep];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kChainStep; ++h) {
             load_rec(a.ws.rec, o[h], r[h][0], r[h][1], r[h][2], r[h][3]);
             q[h][0] = __ldg(a.ws.rec2 + 2 * o[h]);
             q[h][1] = __ldg(a.ws.rec2 + 2 * o[h] + 1);
@@ -389,17 +491,12 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb) {
             wk[h] = kChain ? (wi ? __ldg(wi + e) : swk[e * NT + tid]) : 0.0f;
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kChainStep; ++h) {
             const int e = e0 + h;
             if (e < n) {
-                const float4 J = jst[e * NT + tid];
                 const Trace tr = trace_px(r[h][0], r[h][1], r[h][2], r[h][3], px, py);
-                const float ea = ex2_approx(-0.5f * kLog2e * tr.qb * rcp_approx(tr.b));
-                const float er = sqrt_approx(0.5f * tr.b);
-                const float dqt = fmaf(J.w, inv2tau, -0.25f * ea * J.x);
-                const float db = J.z * rcp_approx(4.0f * er);
                 float gv[9];
-                chain_to_camera(q[h][0], q[h][1], tr, r[h][3], invF, dqt, J.y, db, gv);
+                chain_to_camera(q[h][0], q[h][1], tr, r[h][3], invF, J[h].x, J[h].y, J[h].z, gv);
                 float* gc = a.ws.gcam + kGcamStride * o[h];
                 red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
                 red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
@@ -432,28 +529,126 @@ __global__ void __launch_bounds__(16 * TH, TH == 16 ? 2 : (KM <= 20 ? 4 : 3)) k_
         const ViewDesc& vd = a.views[view_of_tile(a.views, a.hdr->nviews, t)];
         const int C = vd.C;
         if ((C >= 8) != WIDE) continue;
-        if (WIDE) backward_tile<KM, TH, kAttrWarp>(a, t, hb);
-        else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t, hb);
-        else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t, hb);
-        else backward_tile<KM, TH, kAttrSlot>(a, t, hb);
+        if (WIDE) backward_tile<KM, TH, kAttrWarp>(a, t, hb, threadIdx.x >> 5);
+        else if (C >= 4) backward_tile<KM, TH, kAttrLane>(a, t, hb, threadIdx.x >> 5);
+        else if (vd.weights_in || (wk_in_smem<KM, TH>() && a.wk_smem)) backward_tile<KM, TH, kAttrChain>(a, t, hb, threadIdx.x >> 5);
+        else backward_tile<KM, TH, kAttrSlot>(a, t, hb, threadIdx.x >> 5);
     }
 }
 
 // The fitting step's backward (the forward's W_k supplied, C <= 3, lists of
 // up to 20): every tile takes the packed set-up.
+// Row pairs (units) of a backward tile with at least one kept entry, for the
+// packed form.  A block takes 256 consecutive units, each of its warps 32 of
+// them: lane x first works out where unit x's lists are, then the warp reads
+// the first list entry of each unit's 32 pixels, all 32 units at once, and a
+// ballot tells whether any is kept.  The block appends its live units in
+// order with one atomic.
+__global__ void __launch_bounds__(256) k_live_units(Args a) {
+    constexpr int TH = 8, Q = TH / 2, kAhead = 32;
+    __shared__ unsigned s_mask[8];
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
+    const int first = Q * R * a.hdr->class_begin[a.cls], end = Q * R * a.hdr->class_end[a.cls];
+    const int r = lane >> 4, c = lane & 15;
+    for (int ub = first + 256 * blockIdx.x; ub < end; ub += 256 * gridDim.x) {
+        // this lane's unit: view, first list word, row stride, rows and columns inside the image
+        const int u = ub + 32 * w + lane;
+        int v = 0, Wu = 0, Lu = 0, nrows = 0, ncols = 0;
+        const int32_t* base = nullptr;
+        if (u < end) {
+            const int tb = u / Q, q = u - tb * Q, t = tb / R, hb = tb - t * R;
+            v = view_of_tile(a.views, a.hdr->nviews, t);
+            const ViewDesc& vd = a.views[v];
+            const int lt = t - vd.tile_base;
+            const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
+            const int row0 = ty * vd.tile_h + hb * TH + 2 * q, col0 = tx * kTileW;
+            Wu = vd.W;
+            Lu = vd.L;
+            nrows = max(0, min(2, vd.H - row0));
+            ncols = min(kTileW, vd.W - col0);
+            base = vd.index_in + ((int64_t)row0 * vd.W + col0) * vd.L;
+        }
+        unsigned mask = 0u;  // bit x: unit ub + 32 w + x is live
+#pragma unroll 1
+        for (int x0 = 0; x0 < 32; x0 += kAhead) {
+            int32_t g[kAhead];
+#pragma unroll
+            for (int h = 0; h < kAhead; ++h) {
+                const int x = x0 + h;
+                const int32_t* bx = reinterpret_cast<const int32_t*>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(base), x));
+                const int wx = __shfl_sync(0xffffffffu, Wu, x), lx = __shfl_sync(0xffffffffu, Lu, x);
+                const int nr = __shfl_sync(0xffffffffu, nrows, x), nc = __shfl_sync(0xffffffffu, ncols, x);
+                g[h] = (r < nr && c < nc) ? __ldg(bx + ((int64_t)r * wx + c) * lx) : -1;
+            }
+#pragma unroll
+            for (int h = 0; h < kAhead; ++h)
+                if (__any_sync(0xffffffffu, g[h] >= 0)) mask |= 1u << (x0 + h);
+        }
+        if (lane == 0) s_mask[w] = mask;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int n = 0;
+#pragma unroll
+            for (int x = 0; x < 8; ++x) n += __popc(s_mask[x]);
+            s_base = n ? atomicAdd(&a.ws.live_hdr->n[a.cls], n) : 0;
+        }
+        __syncthreads();
+        if ((mask >> lane) & 1u) {
+            int pos = s_base + __popc(mask & ((1u << lane) - 1u));
+            for (int x = 0; x < w; ++x) pos += __popc(s_mask[x]);
+            a.ws.live[first + pos] = make_int2(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// Warp-persistent over the units: each warp claims units one at a time (two
+// claims ahead), with no block barriers, and stages the next unit's lists
+// while the current one's pair terms and chain rule run.  When the call's
+// record of live units describes these lists (the forward's, or
+// k_live_units'), only those are visited; otherwise every unit of the class
+// is, and the empty ones cost their list read.
 template <int KM>
 __global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
-    __shared__ int s_slot;
-    constexpr int TH = 8;
+    constexpr int TH = 8, Q = TH / 2;
+    extern __shared__ float4 smem[];
+    int32_t* sid = reinterpret_cast<int32_t*>(smem + KM * 16 * TH);
+    const int lane = threadIdx.x & 31;
     const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
-    for (;;) {
-        if (threadIdx.x == 0) s_slot = atomicAdd(&a.hdr->counters[a.cls + kMaxClasses], 1);
-        __syncthreads();
-        const int tb = R * a.hdr->class_begin[a.cls] + s_slot;
-        __syncthreads();
-        if (tb >= R * a.hdr->class_end[a.cls]) return;
-        const int t = tb / R, hb = tb - t * R;
-        backward_tile<KM, TH, kAttrPacked>(a, t, hb);
+    int* counter = &a.hdr->counters[a.cls + kMaxClasses];
+    const int first = Q * R * a.hdr->class_begin[a.cls];
+    const LiveHdr* lh = a.ws.live_hdr;
+    const bool rec = lh->index_fwd != nullptr && lh->index_fwd == a.views[0].index_in;
+    const int count = rec ? lh->n[a.cls] : Q * R * a.hdr->class_end[a.cls] - first;
+    const int2* live = a.ws.live + first;
+    auto unit = [&](int x) -> int2 {
+        if (rec) return __ldg(live + x);
+        return make_int2(first + x, view_of_tile(a.views, a.hdr->nviews, (first + x) / (Q * R)));
+    };
+    auto stage = [&](int2 un) {
+        const int tb = un.x / Q, t = tb / R;
+        stage_lists_packed<TH>(a, sid, un.y, t, tb - t * R, un.x - tb * Q);
+    };
+    int cur = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(counter, 1) : 0, 0);
+    int2 cu = make_int2(0, 0);
+    if (cur < count) {
+        cu = unit(cur);
+        stage(cu);
+    }
+    int claim = lane == 0 ? atomicAdd(counter, 1) : 0;
+    while (cur < count) {
+        const int nx = __shfl_sync(0xffffffffu, claim, 0);
+        const int2 nu = nx < count ? unit(nx) : make_int2(0, 0);
+        claim = lane == 0 ? atomicAdd(counter, 1) : 0;
+        const int tb = cu.x / Q, t = tb / R;
+        backward_tile<KM, TH, kAttrPacked>(a, t, tb - t * R, cu.x - tb * Q, cu.y, [&]() {
+            if (nx < count) stage(nu);
+        });
+        cur = nx;
+        cu = nu;
     }
 }
 
@@ -609,7 +804,14 @@ static cudaError_t launch_backward_pair(const char* name, const char* wname, int
 
 // The packed form (k_backward_packed) for capacities up to 20, when every
 // view brings the forward's weights and C <= 3.
-cudaError_t launch_backward_packed(int KM, int nblocks, cudaStream_t s, const Args& a) {
+cudaError_t launch_backward_packed(int KM, int nblocks, int live_tiles, cudaStream_t s, const Args& a) {
+    if (live_tiles > 0) {  // find the live units of given lists
+        TraceScope tr("k_live_units", s);
+        const int nb = (8 * live_tiles + 255) / 256;  // at most 8 units per tile
+        k_live_units<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(a);
+        const cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) return e;
+    }
     switch (KM) {
         case 8: return launch_tiles(k_backward_packed<8>, "k_backward<8>", nblocks, 128, backward_smem_bytes<8, 8>(), s, a);
         case 16: return launch_tiles(k_backward_packed<16>, "k_backward<16>", nblocks, 128, backward_smem_bytes<16, 8>(), s, a);

@@ -108,6 +108,20 @@ struct BatchHdr {
 };
 static_assert(sizeof(BatchHdr) % 16 == 0, "BatchHdr layout");
 
+// A record of the row pairs (units: rows 2q, 2q + 1 of a 16 x 8 backward
+// tile, one warp of a tile launch) whose index lists keep an entry, in device
+// memory just after the view table: written by the forward pass as it
+// selects, or by k_live_units from given lists.  Every upload clears it and
+// names the lists it will describe (null: none); a backward that reuses the
+// forward's projection uploads only the header and view table, so it finds
+// the forward's record, and uses it when it reads those same lists.
+struct LiveHdr {
+    int32_t n[kMaxClasses];      // units in the list, per class
+    const int32_t* index_fwd;    // the lists they describe (view 0's first word)
+    int64_t pad;
+};
+static_assert(sizeof(LiveHdr) % 16 == 0, "LiveHdr layout");
+
 // ------------------------------------------------------------------------
 // Checked builds (-DVOGE_CHECKED, build.py's checked library): every gather
 // and scatter index of the tile kernels goes through VOGE_IDX.  An index
@@ -414,6 +428,20 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                  : "memory");
 }
 
+// Asynchronous global -> shared copies (PTX cp.async, sm_80+): 16 bytes
+// through L2 only, or 4 bytes through L1; a thread waits for its own groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // View of a global tile / record / image element (binary searches over the
 // view table's monotone bases).
 __device__ __forceinline__ int view_of_tile(const ViewDesc* __restrict__ vd, int nv, int tile) {
@@ -457,6 +485,8 @@ struct Ws {
     float* gcam;      // [records][12] backward accumulators: dM (3), G (6), narrow attribute gradient (3)
     float* gkey;      // generic-path per-pixel scratch
     int32_t* gid;
+    int2* live;       // (unit, view) of each row pair with a kept entry (class c from (TH/2) class_begin[c])
+    LiveHdr* live_hdr;  // their count (null: not recorded)
     int32_t gen_L;    // list length the generic scratch is laid out for
 };
 

@@ -516,6 +516,12 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             atomicAdd(&a.hdr->traces, (unsigned long long)w_traced);
             atomicAdd(&a.hdr->entries, (unsigned long long)w_entries);
             atomicAdd(&a.hdr->pairs, (unsigned long long)w_pairs);
+            // this warp's row pair is a live unit of the backward (unit
+            // numbering: TH / 2 per tile, the warps of a tile in order)
+            if (w_entries > 0 && a.ws.live_hdr) {
+                const int pos = atomicAdd(&a.ws.live_hdr->n[a.cls], 1);
+                a.ws.live[(TH / 2) * a.hdr->class_begin[a.cls] + pos] = make_int2((TH / 2) * t + (tid >> 5), v);
+            }
         }
     }
     // The lists are sorted; the selection buffers are free from here on.
@@ -580,17 +586,6 @@ struct FineSmem {
     static constexpr size_t bytes = SegScratch<KM>::bytes + 2 * buf;
 };
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Row r of group g: its view, tile column and image row.
 struct FineRow {

@@ -335,6 +335,49 @@ def test_reuse_projection_matches():
         assert rel_err(x, y) < 1e-5
 
 
+def test_packed_backward_with_the_forwards_record_of_live_row_pairs():
+    """The fitting step's backward (forward weights, C <= 3, K <= 20: the packed
+    form) over the forward's own lists with the projection reused takes the
+    forward's record of which 16 x 2-pixel row pairs kept an entry.  Its
+    gradients match the oracle and a backward that finds those row pairs itself
+    (the lists copied, or the projection recomputed), on ragged views whose
+    edges cut tiles and row pairs."""
+    voge = lib_ready()
+    rng = np.random.default_rng(22)
+    N = 1200
+    means = r32(np.concatenate([rng.uniform(-1, 1, (N, 2)), rng.uniform(3, 5, (N, 1))], 1))
+    inv_cov = r32(scenes.inverse_covariance(scenes.random_rotations(rng, N),
+                                            np.exp(rng.normal(np.log(0.06), 0.3, (N, 3)))))
+    attr = r32(rng.uniform(0, 1, (N, 3)))
+    cams = [{"R": np.eye(3), "T": np.zeros(3), "F": 45.0, "Ox": 30.5, "Oy": 21.5, "H": 43, "W": 61},
+            {"R": np.eye(3), "T": np.zeros(3), "F": 38.0, "Ox": 17.5, "Oy": 33.5, "H": 67, "W": 35}]
+    r = voge.Renderer(cams, N, 3, K=20, tau=1.0, thresh=0.005)
+    m, p, a = to_dev(means), to_dev(inv_cov), to_dev(attr)
+    img, w, idx = r.forward(m, p, a)
+    g = to_dev(np.random.default_rng(23).standard_normal(tuple(img.shape)))
+
+    def run(index, weights, reuse):
+        gm, gp, ga = torch.zeros_like(m), torch.zeros_like(p), torch.zeros_like(a)
+        gc = torch.zeros((2, 12), device="cuda")
+        r.backward(m, p, a, index, g, gm, gp, ga, gc, reuse_projection=reuse, weights=weights)
+        torch.cuda.synchronize()
+        gcn = gc.cpu().numpy()
+        return {"g_means": gm.cpu().numpy(), "g_inv_cov": gp.cpu().numpy(), "g_attr": ga.cpu().numpy(),
+                "g_R": gcn[:, :9].reshape(-1, 3, 3), "g_T": gcn[:, 9:]}
+
+    own = run(idx, w, True)
+    copied = run(idx.clone(), w.clone(), True)
+    r.forward(m, p, a, out=(img, w, idx))
+    recomputed = run(idx, w, False)
+    L = r.L
+    want = oracle.render_bwd(cams, means, inv_cov, attr, 1.0, oracle.all_pixels(cams),
+                             idx.cpu().numpy()[:, :L], g.cpu().numpy())
+    check_grads(own, want)
+    for other in (copied, recomputed):
+        for k in own:
+            assert rel_err(other[k], own[k]) <= 1e-5, k
+
+
 def test_pose_gradient_kernel():
     voge = lib_ready()
     rng = np.random.default_rng(16)
