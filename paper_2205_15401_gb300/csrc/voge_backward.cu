@@ -54,20 +54,27 @@ constexpr int kAttrLane = 0, kAttrWarp = 1, kAttrChain = 2, kAttrSlot = 3, kAttr
 template <int KM, int TH>
 __host__ __device__ constexpr bool wk_in_smem() { return KM <= 20; }
 
-// Packed backward: the calling warp's asynchronous copies of the index
-// lists of unit (t, hb, q) of view v, transposed on the way into its columns
-// of sid ([list position][pixel of the block]): word x of a row's [16][L]
-// block is list position x % L of column x / L (L <= 20 < 32, so one carry
-// per step).  Pixels outside the image are never read.  One commit group.
-template <int TH>
-__device__ __forceinline__ void stage_lists_packed(const Args& a, int32_t* sid, int v, int t, int hb, int q) {
-    constexpr int NT = 16 * TH;
+// Packed backward: index lists staged per warp as [pixel of the row pair]
+// [stride], stride = L rounded up to odd, so that lanes reading one list
+// position of their pixels hit distinct banks.
+__host__ __device__ constexpr int packed_stride(int L) { return L | 1; }
+template <int KM>
+__host__ __device__ constexpr int packed_warp_words() { return 32 * packed_stride(KM); }
+
+// The calling warp's asynchronous copies of the index lists of unit
+// (t, hb, q) of view v into its staging rows sw: consecutive lanes take
+// consecutive words of a row segment's [16][L] block (word x is list position
+// x % L of column x / L; L <= 20 < 32, so one carry per step), landing on
+// consecutive words of sw.  Pixels outside the image are never read.  One
+// commit group.
+__device__ __forceinline__ void stage_lists_packed(const Args& a, int32_t* sw, int v, int t, int hb, int q) {
+    constexpr int TH = 8;
     const ViewDesc& vd = a.views[v];
     const int lt = t - vd.tile_base;
     const int tx = lt % vd.tiles_x, ty = lt / vd.tiles_x;
-    const int H = vd.H, W = vd.W, L = vd.L;
+    const int H = vd.H, W = vd.W, L = vd.L, S = packed_stride(L);
     const int row0 = ty * vd.tile_h + hb * TH + 2 * q;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int ncols = min(kTileW, W - tx * kTileW);
     const int dc = 32 / L, dk = 32 - dc * L;
 #pragma unroll
@@ -78,9 +85,9 @@ __device__ __forceinline__ void stage_lists_packed(const Args& a, int32_t* sid, 
         if (cnt > 0) o0 = VOGE_IDX(a.hdr, o0 + cnt - 1, (int64_t)H * W * L, kChkListRead) - (cnt - 1);
         const int32_t* src = vd.index_in + o0;
         int col = lane / L, k = lane - col * L;
-        int32_t* dst = sid + 32 * warp + 16 * rw;
+        int32_t* dst = sw + 16 * rw * S;
         for (int x = lane; x < cnt; x += 32) {
-            cp_async4(dst + k * NT + col, src + x);
+            cp_async4(dst + col * S + k, src + x);
             k += dk;
             col += dc;
             if (k >= L) {
@@ -100,11 +107,14 @@ struct NoHook {
 // binning tile t of view v (v < 0: looked up) -- the backward reads the index
 // lists, not the tile lists, so it may split the forward's tiles into shorter
 // ones -- for the calling warp, in its warp's shared-memory columns.  The
-// packed form finds its lists already staged in sid (stage_lists_packed) and
-// calls next() once, as soon as sid is free again, so that the caller can
-// stage its next unit while this one runs.
-template <int KM, int TH, int AM, typename Hook = NoHook>
-__device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int q, int v = -1, Hook next = Hook()) {
+// packed form finds its lists already staged in its warp's rows of the W_k
+// buffer (stage_lists_packed).  The set-up replaces them with the entries'
+// dA_k; once those are in registers, restage() copies this unit's lists in
+// again (they arrive during the pair terms), and once the chain rule has
+// taken the indices into the stream, next() may stage the caller's next unit.
+template <int KM, int TH, int AM, typename Restage = NoHook, typename Hook = NoHook>
+__device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int q, int v = -1,
+                                              Restage restage = Restage(), Hook next = Hook()) {
     constexpr int NT = 16 * TH;
     extern __shared__ float4 smem[];
     float4* jst = smem;  // [KM][NT]
@@ -134,8 +144,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
     // staged index lists of the packed set-up, in the layout of the W_k
     // buffer, which takes each entry's dA_k in place of its index once the
     // entry is set up
-    int32_t* sid = reinterpret_cast<int32_t*>(swk);
     const int lane = tid & 31, warp = tid >> 5;
+    const int S = packed_stride(L);
+    int32_t* sw = reinterpret_cast<int32_t*>(swk) + warp * packed_warp_words<KM>();  // this warp's rows
     auto stg = [&](int x) -> int32_t* {
         return reinterpret_cast<int32_t*>(jst + (x >> 7) * NT + 32 * warp) + (x & 127);
     };
@@ -157,9 +168,9 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
     }
     __syncwarp();
     // a warp whose 32 lists are all empty has nothing to add
-    if (!__any_sync(0xffffffffu, valid && (packed ? sid[tid] : *stg(lane * L)) >= 0)) {
+    if (!__any_sync(0xffffffffu, valid && (packed ? sw[lane * S] : *stg(lane * L)) >= 0)) {
         if constexpr (packed) {
-            __syncwarp();  // every lane has read sid
+            __syncwarp();  // every lane has read its row
             next();
         }
         return;
@@ -184,13 +195,13 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
         // lanes take neighbouring pixels at one position -- distinct shared-
         // memory banks, and often the same record.  Each entry's (l, r, m)
         // goes to the stream and dA_k replaces its staged index.
-        float* sdA = swk;
+        float* sdA = reinterpret_cast<float*>(sw);
         {
             bool open = valid;
 #pragma unroll
             for (int s = 0; s < KM; ++s) {
                 if (s < K) {
-                    const int32_t g = sid[s * NT + tid];
+                    const int32_t g = sw[lane * S + s];
                     open = open && g >= 0 && g < N;
                     n += open ? 1 : 0;
                 }
@@ -242,7 +253,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
                 // a lane past the last entry reads no staged index (its owner
                 // may already have replaced it) and gathers record 0
                 gg[h] = i0 + 32 * h + lane < total
-                            ? (int32_t)VOGE_IDX(a.hdr, sid[k * NT + 32 * warp + p], N, kChkRecord)
+                            ? (int32_t)VOGE_IDX(a.hdr, sw[p * S + k], N, kChkRecord)
                             : 0;
             }
             float4 r[kSetupStep][4];
@@ -269,7 +280,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
                     const Entry e = entry_px(r[h][0], r[h][1], r[h][2], r[h][3], pxp, pyp);
                     const float G = fmaf(gq[h][2], c[h][2], fmaf(gq[h][1], c[h][1], gq[h][0] * c[h][0]));
                     jst[kk[h] * NT + 32 * warp + p] = make_float4(e.hi, e.lo, e.r, 0.5f * e.a);
-                    sdA[kk[h] * NT + 32 * warp + p] = -tau * G * wk[h];
+                    sdA[p * S + kk[h]] = -tau * G * wk[h];
                 }
             }
         }
@@ -282,15 +293,15 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
                 const float4 J = jst[e * NT + tid];
                 hi[s] = J.x;
                 lo[s] = J.y;
-                dA[s] = sdA[e * NT + tid];
+                dA[s] = sdA[lane * S + e];
             } else {
                 hi[s] = 0.0f;
                 lo[s] = 0.0f;
                 dA[s] = 0.0f;
             }
         }
-        __syncwarp();  // every lane has read its dA_k: sid is free
-        next();
+        __syncwarp();  // every lane has read its dA_k: the rows are free
+        restage();
     } else if (early && valid) {
         const float* gp0 = vd.grad_image + pix * C;
         ga0 = __ldg(gp0);
@@ -418,7 +429,7 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
             }
         }
     }
-    if (n == 0) return;  // no warp-wide steps below
+    if (!packed && n == 0) return;  // no warp-wide steps below (the packed form has some)
     // loop 2: adjoint of the pair terms
     for (int e = 0; e < n; ++e) {
         const float4 J = jst[e * NT + tid];
@@ -448,8 +459,17 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
     const float inv2tau = 0.5f / tau;
     {
         int32_t gid[KM];
+        if constexpr (packed) {
+            cp_async_wait<0>();  // this unit's lists, staged again
+            __syncwarp();
 #pragma unroll
-        for (int s = 0; s < KM; ++s) gid[s] = kept(s) ? __ldg(li + (s - (KM - K))) : 0;
+            for (int s = 0; s < KM; ++s) gid[s] = kept(s) ? sw[lane * S + (s - (KM - K))] : 0;
+            __syncwarp();  // every lane has its indices: the rows are free
+            next();
+        } else {
+#pragma unroll
+            for (int s = 0; s < KM; ++s) gid[s] = kept(s) ? __ldg(li + (s - (KM - K))) : 0;
+        }
         int e = 0;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
@@ -615,7 +635,7 @@ template <int KM>
 __global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
     constexpr int TH = 8, Q = TH / 2;
     extern __shared__ float4 smem[];
-    int32_t* sid = reinterpret_cast<int32_t*>(smem + KM * 16 * TH);
+    int32_t* sw = reinterpret_cast<int32_t*>(smem + KM * 16 * TH) + (threadIdx.x >> 5) * packed_warp_words<KM>();
     const int lane = threadIdx.x & 31;
     const int R = max(1, a.views[view_of_tile(a.views, a.hdr->nviews, a.hdr->class_begin[a.cls])].tile_h / TH);
     int* counter = &a.hdr->counters[a.cls + kMaxClasses];
@@ -630,7 +650,7 @@ __global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
     };
     auto stage = [&](int2 un) {
         const int tb = un.x / Q, t = tb / R;
-        stage_lists_packed<TH>(a, sid, un.y, t, tb - t * R, un.x - tb * Q);
+        stage_lists_packed(a, sw, un.y, t, tb - t * R, un.x - tb * Q);
     };
     int cur = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(counter, 1) : 0, 0);
     int2 cu = make_int2(0, 0);
@@ -644,9 +664,11 @@ __global__ void __launch_bounds__(128, 4) k_backward_packed(Args a) {
         const int2 nu = nx < count ? unit(nx) : make_int2(0, 0);
         claim = lane == 0 ? atomicAdd(counter, 1) : 0;
         const int tb = cu.x / Q, t = tb / R;
-        backward_tile<KM, TH, kAttrPacked>(a, t, tb - t * R, cu.x - tb * Q, cu.y, [&]() {
-            if (nx < count) stage(nu);
-        });
+        backward_tile<KM, TH, kAttrPacked>(
+            a, t, tb - t * R, cu.x - tb * Q, cu.y, [&]() { stage(cu); },
+            [&]() {
+                if (nx < count) stage(nu);
+            });
         cur = nx;
         cu = nu;
     }
@@ -771,6 +793,12 @@ static size_t backward_smem_bytes(bool = true) {
     return (size_t)KM * 16 * TH * (wk_in_smem<KM, TH>() ? 20 : 16);
 }
 
+// The packed form: the stream, then each warp's staging rows.
+template <int KM>
+static size_t packed_smem_bytes() {
+    return (size_t)KM * 16 * 8 * 16 + 4 * (size_t)packed_warp_words<KM>() * 4;
+}
+
 template <typename Kern>
 static int blocks_per_sm(Kern k, int nthreads, size_t smem) {
     if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -813,9 +841,9 @@ cudaError_t launch_backward_packed(int KM, int nblocks, int live_tiles, cudaStre
         if (e != cudaSuccess) return e;
     }
     switch (KM) {
-        case 8: return launch_tiles(k_backward_packed<8>, "k_backward<8>", nblocks, 128, backward_smem_bytes<8, 8>(), s, a);
-        case 16: return launch_tiles(k_backward_packed<16>, "k_backward<16>", nblocks, 128, backward_smem_bytes<16, 8>(), s, a);
-        case 20: return launch_tiles(k_backward_packed<20>, "k_backward<20>", nblocks, 128, backward_smem_bytes<20, 8>(), s, a);
+        case 8: return launch_tiles(k_backward_packed<8>, "k_backward<8>", nblocks, 128, packed_smem_bytes<8>(), s, a);
+        case 16: return launch_tiles(k_backward_packed<16>, "k_backward<16>", nblocks, 128, packed_smem_bytes<16>(), s, a);
+        case 20: return launch_tiles(k_backward_packed<20>, "k_backward<20>", nblocks, 128, packed_smem_bytes<20>(), s, a);
         default: return cudaErrorInvalidValue;
     }
 }
