@@ -346,15 +346,24 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
     }
     const int32_t* li = vd.index_in + pix * L;
     auto kept = [&](int s) { return s >= KM - K && s - (KM - K) < n; };
+    // depths relative to the pixel's nearest kept entry, l - l0 = (hi - l0) + lo
+    // with l0 = hi of list position 0: the pair terms take l_k - l_j as one
+    // difference of these, and the k side holds one register per slot (a lane
+    // with an empty list runs no pair loop, so its l0 is never used)
+    const float l0 = jst[tid].x;
+    float dk[KM];
+#pragma unroll
+    for (int s = 0; s < KM; ++s) dk[s] = (hi[s] - l0) + lo[s];
     // loop 1: A_k (skipped when the forward's W_k are supplied)
     float A[KM];
 #pragma unroll
     for (int s = 0; s < KM; ++s) A[s] = 0.0f;
     for (int e = 0; e < (wi ? 0 : n); ++e) {
         const float4 J = jst[e * NT + tid];
+        const float dj = (J.x - l0) + J.y;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
-            const float u = ((hi[s] - J.x) + (lo[s] - J.y)) * J.z;
+            const float u = (dk[s] - dj) * J.z;
             const float q = erfc_as28(fabsf(u));
             const float sm = copysignf(J.w, u);
             A[s] = fmaf(-sm, q, A[s] + (J.w + sm));
@@ -434,10 +443,11 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
     for (int e = 0; e < n; ++e) {
         const float4 J = jst[e * NT + tid];
         const float mj = J.w * kTwoOverSqrtPi;
+        const float dj = (J.x - l0) + J.y;
         float acc_dm = 0.0f, acc_s = 0.0f, acc_dr = 0.0f;
 #pragma unroll
         for (int s = 0; s < KM; ++s) {
-            const float d = (hi[s] - J.x) + (lo[s] - J.y);
+            const float d = dk[s] - dj;
             const float u = d * J.z;
             float g2;
             const float ec = erfc_as26(fabsf(u), g2);

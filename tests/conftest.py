@@ -29,9 +29,9 @@ def pytest_collection_modifyitems(config, items):
 
 def pytest_terminal_summary(terminalreporter):
     """Lists that differ from the oracle's at allowed FP32/FP64 ties, per
-    forward check, and each gradient check's margins."""
+    forward check, and each forward and gradient check's margins."""
     try:
-        from parity import GRAD_STATS, LIST_DIFFS
+        from parity import FWD_ERRS, GRAD_STATS, LIST_DIFFS
     except Exception:  # pragma: no cover
         return
     tr = terminalreporter
@@ -39,6 +39,10 @@ def pytest_terminal_summary(terminalreporter):
         tr.section("index lists differing at allowed ties")
         for name, n_diff, total in LIST_DIFFS:
             tr.write_line(f"{n_diff:6d} of {total:8d}  {name}")
+    if FWD_ERRS:
+        tr.section("forward parity: worst |image - oracle| and |W - oracle| (bound 1e-4)")
+        for name, ei, ew in FWD_ERRS:
+            tr.write_line(f"{ei:9.2e} {ew:9.2e}  {name}")
     if GRAD_STATS:
         tr.section("gradient parity: relative norm error (bound 1e-3), worst per-element error / its bound")
         for name, key, rel, exc in GRAD_STATS:

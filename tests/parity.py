@@ -71,6 +71,8 @@ def check_lists(gpu_idx, ref, cams, means, inv_cov, attr, K, tau, eta):
 # and (test, tensor, relative error, per-element excess) of every gradient
 # check in the session; conftest prints them at the end of the run
 LIST_DIFFS = []
+# (test, worst |image - oracle|, worst |W - oracle|) of each forward check
+FWD_ERRS = []
 GRAD_STATS = []
 
 
@@ -82,10 +84,10 @@ def check_forward(image, weights, index, cams, means, inv_cov, attr, K, tau, eta
     LIST_DIFFS.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], n_diff, int(ref["idx"].shape[0])))
     fine = oracle.fine(cams, means, inv_cov, attr, tau, ref["pix"], index)
     err_img = np.abs(image - fine["image"]).max() if image.size else 0.0
+    err_w = np.abs(weights - fine["weights"]).max() if weights is not None and weights.size else 0.0
+    FWD_ERRS.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], float(err_img), float(err_w)))
     assert err_img <= TOL_IMAGE, f"image error {err_img}"
-    if weights is not None and weights.size:
-        err_w = np.abs(weights - fine["weights"]).max()
-        assert err_w <= TOL_IMAGE, f"weight error {err_w}"
+    assert err_w <= TOL_IMAGE, f"weight error {err_w}"
     return {"ref": ref, "n_diff": n_diff, "err_image": float(err_img), "covered": int((ref["count"] > 0).sum())}
 
 
