@@ -439,10 +439,15 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
         }
     }
     if (!packed && n == 0) return;  // no warp-wide steps below (the packed form has some)
-    // loop 2: adjoint of the pair terms
+    // loop 2: adjoint of the pair terms.  1 + erf u is formed as 1 + E with
+    // E = copysign(1 - erfc|u|, u), so that a k in front of j adds dA_k
+    // erfc|u| without cancellation.  The factor m_j 2/sqrt(pi) of du is
+    // applied once per j to the j-side sums, and folded into the k side's
+    // per-j factor mz.
     for (int e = 0; e < n; ++e) {
         const float4 J = jst[e * NT + tid];
         const float mj = J.w * kTwoOverSqrtPi;
+        const float mz = mj * J.z;
         const float dj = (J.x - l0) + J.y;
         float acc_dm = 0.0f, acc_s = 0.0f, acc_dr = 0.0f;
 #pragma unroll
@@ -453,11 +458,13 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
             const float ec = erfc_as26(fabsf(u), g2);
             const float E = copysignf(1.0f - ec, u);
             acc_dm = fmaf(dA[s], 1.0f + E, acc_dm);
-            const float du = dA[s] * mj * g2;
-            dl[s] = fmaf(du, J.z, dl[s]);
+            const float du = dA[s] * g2;  // du_kj / (m_j 2/sqrt(pi))
+            dl[s] = fmaf(du, mz, dl[s]);
             acc_s += du;
             acc_dr = fmaf(du, d, acc_dr);
         }
+        acc_s *= mj;
+        acc_dr *= mj;
         // j-side parts of dqt_j = dA_j / (2 tau) - a_j dm_j / 4 (a_j = 2 m_j)
         // and of dl_j; db_j = dr_j / (4 r_j) in full
         jst[e * NT + tid] = make_float4(-0.5f * J.w * acc_dm, -acc_s * J.z, acc_dr * rcp_approx(4.0f * J.z), 0.0f);

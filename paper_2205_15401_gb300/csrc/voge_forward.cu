@@ -222,17 +222,21 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         for (int x = lane; x < ncols * L; x += 32)
             vd.weights[VOGE_IDX(a.hdr, ((int64_t)irow * W + col0) * L + x, (int64_t)H * W * L, kChkOutput)] = Wst[x];
     if (narrow) {
-        // image: each pixel's lane adds W_k c_k over its list, eight rows in flight
-        if (px_ok && lane < 16) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int k0 = 0; k0 < n; k0 += 8) {
+        // image: two lanes per pixel (lane p and p + 16 take its even and odd
+        // list positions), eight rows each in flight, added by one shuffle
+        const int pp = lane & 15, h = lane >> 4;
+        const int np = __shfl_sync(FULL, n, pp);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pp < ncols) {
+            for (int k0 = h; k0 < np; k0 += 16) {
                 float4 c[8];
                 float w[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = min(k0 + u, n - 1);
-                    w[u] = k0 + u < n ? Wst[lane * L + k] : 0.0f;
-                    const float* ap = vd.attr + VOGE_IDX(a.hdr, id_of(lane, k), vd.N, kChkRecord) * C;
+                    const int kk = k0 + 2 * u;
+                    const int k = min(kk, np - 1);
+                    w[u] = kk < np ? Wst[pp * L + k] : 0.0f;
+                    const float* ap = vd.attr + VOGE_IDX(a.hdr, id_of(pp, k), vd.N, kChkRecord) * C;
                     c[u].x = __ldg(ap);
                     c[u].y = C > 1 ? __ldg(ap + 1) : 0.0f;
                     c[u].z = C > 2 ? __ldg(ap + 2) : 0.0f;
@@ -246,7 +250,13 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
                     acc.w = fmaf(w[u], c[u].w, acc.w);
                 }
             }
-            float* ip = img + lane * C;
+        }
+        acc.x += __shfl_down_sync(FULL, acc.x, 16);
+        acc.y += __shfl_down_sync(FULL, acc.y, 16);
+        acc.z += __shfl_down_sync(FULL, acc.z, 16);
+        acc.w += __shfl_down_sync(FULL, acc.w, 16);
+        if (h == 0 && pp < ncols) {
+            float* ip = img + pp * C;
             ip[0] = acc.x;
             if (C > 1) ip[1] = acc.y;
             if (C > 2) ip[2] = acc.z;
