@@ -183,10 +183,14 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
     __syncwarp();
     // sum of m_j over each pixel's list: 1 + erf(u) = 1 + sign(u) erf|u|, so
     // A_k = sum_j m_j + sum_j copysign(m_j, u_kj) (1 - erfc|u_kj|)
-    if (lane < 16) {
+    {
+        // two lanes per pixel (even and odd list positions), one shuffle
+        const int pp = lane & 15;
+        const int np = __shfl_sync(FULL, n, pp), eb = __shfl_sync(FULL, excl, pp);
         float ms = 0.0f;
-        for (int k = 0; k < n; ++k) ms += E[excl + k].w;
-        msum[lane] = ms;
+        for (int k = lane >> 4; k < np; k += 2) ms += E[eb + k].w;
+        ms += __shfl_down_sync(FULL, ms, 16);
+        if (lane < 16) msum[lane] = ms;
     }
     __syncwarp();
     const bool narrow = C <= 4;
@@ -392,15 +396,24 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
         return;
     }
     bool active = valid;
+    // depth bound of the first candidate after the current chunk (sorted
+    // order: it bounds every later one), staged with the chunk by thread 0
+    __shared__ float s_next_bound;
     for (int base = 0; base < src.count; base += NT) {
         const int nc = min(NT, src.count - base);
+        const bool has_next = src.mode == 1 && nc == NT && base + NT < src.count;
         if (tid < nc) {
-            int32_t g;
+            int32_t g, gn = 0;
             if (src.mode != 2) g = a.ws.tile_gauss[VOGE_IDX(a.hdr, src.start + base + tid, a.ws.bin_cap, kChkTileList)];
             else g = base + tid;
+            if (tid == 0 && has_next)
+                gn = (int32_t)VOGE_IDX(
+                    a.hdr, __ldg(a.ws.tile_gauss + VOGE_IDX(a.hdr, src.start + base + NT, a.ws.bin_cap, kChkTileList)), vd.N,
+                    kChkRecord);
             g = (int32_t)VOGE_IDX(a.hdr, g, vd.N, kChkRecord);
             float4 r0, r1, r2, r3;
             load_rec(a.ws.rec, vb + g, r0, r1, r2, r3);
+            if (tid == 0 && has_next) s_next_bound = __ldg(&a.ws.rec[4 * (vb + gn) + 3].w);
             bool outside = false;
             if (src.filter_box) {
                 const int4 tb = a.ws.tbox[vb + g];
@@ -506,14 +519,7 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
             }
             // a pixel whose list is full and whose next candidate (in sorted
             // order) starts beyond its K-th depth can stop for good
-            if (active && src.mode == 1 && nc == NT && base + NT < src.count) {
-                // the first candidate of the next chunk bounds everything after it
-                const int32_t gn = (int32_t)VOGE_IDX(
-                    a.hdr, __ldg(a.ws.tile_gauss + VOGE_IDX(a.hdr, src.start + base + NT, a.ws.bin_cap, kChkTileList)), vd.N,
-                    kChkRecord);
-                const float nxt = __ldg(&a.ws.rec[4 * (vb + gn) + 3].w);
-                if (nxt > kbar) active = false;
-            }
+            if (active && has_next && s_next_bound > kbar) active = false;
         }
         if (__syncthreads_and(!active)) break;
     }
