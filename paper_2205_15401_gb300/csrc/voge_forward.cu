@@ -96,7 +96,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 template <int KM>
 struct SegScratch {  // per warp
     static constexpr int kItems = 16 * KM;
-    static constexpr size_t e_off = 0;                            // float4 E[kItems]: (hi, lo, r, m)
+    static constexpr size_t e_off = 0;                            // float4 E[KM][16]: (hi, lo, r, m)
     static constexpr size_t w_off = (size_t)kItems * 16;          // float Wst[16][L]
     static constexpr size_t b_off = w_off + (size_t)kItems * 4;   // int pbase[16], pcnt[16]; float msum[16]
     static constexpr size_t bytes = b_off + 192;
@@ -160,23 +160,59 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         pcnt[lane] = n;
     }
     __syncwarp();
-    // entries, 64 at a time (two per lane, their records in flight together)
+    // Set-up, 64 entries at a time (two per lane, their records in flight
+    // together).  The entries are taken by list position first -- row k holds
+    // the pixels whose lists are longer than k (mask M_k, lane k holds it and
+    // the number of entries before row k) -- so that neighbouring lanes take
+    // neighbouring pixels at one position, which often keep the same kernel:
+    // their record gathers share lines.  E is stored the same way, E[k][p].
+    unsigned mrow = 0u;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const unsigned m = __ballot_sync(FULL, n > k);
+        if (lane == k) mrow = m;
+    }
+    const int crow = __popc(mrow);
+    int rincl = crow;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(FULL, rincl, d);
+        if (lane >= d) rincl += t;
+    }
+    const int rexcl = rincl - crow;
     for (int i0 = 0; i0 < total; i0 += 64) {
         float4 r[2][4];
-        int pp[2];
+        int pp[2], kk[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int i = min(i0 + 32 * h + lane, total - 1);
-            pp[h] = pixel_of(i);
-            const int64_t g = VOGE_IDX(a.hdr, id_of(pp[h], i - pbase[pp[h]]), vd.N, kChkRecord);
+            int k = 0;  // the last row whose first entry is at or before i
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int b = __shfl_sync(FULL, rexcl, k + step);
+                if (k + step < KM && b <= i) k += step;
+            }
+            unsigned m = __shfl_sync(FULL, mrow, k);
+            int rr = i - __shfl_sync(FULL, rexcl, k), p = 0;  // the rr-th set bit of M_k
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1) {
+                const int c = __popc(m & ((1u << w) - 1u));
+                if (rr >= c) {
+                    rr -= c;
+                    m >>= w;
+                    p += w;
+                }
+            }
+            pp[h] = p;
+            kk[h] = k;
+            const int64_t g = VOGE_IDX(a.hdr, id_of(p, k), vd.N, kChkRecord);
             load_rec(a.ws.rec, vb + g, r[h][0], r[h][1], r[h][2], r[h][3]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int i = i0 + 32 * h + lane;
-            if (i < total) {
+            if (i0 + 32 * h + lane < total) {
                 const Entry en = entry_px(r[h][0], r[h][1], r[h][2], r[h][3], (float)(col0 + pp[h]) + 0.5f, py);
-                E[i] = make_float4(en.hi, en.lo, en.r, 0.5f * en.a);
+                E[kk[h] * 16 + pp[h]] = make_float4(en.hi, en.lo, en.r, 0.5f * en.a);
             }
         }
     }
@@ -186,9 +222,9 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
     {
         // two lanes per pixel (even and odd list positions), one shuffle
         const int pp = lane & 15;
-        const int np = __shfl_sync(FULL, n, pp), eb = __shfl_sync(FULL, excl, pp);
+        const int np = __shfl_sync(FULL, n, pp);
         float ms = 0.0f;
-        for (int k = lane >> 4; k < np; k += 2) ms += E[eb + k].w;
+        for (int k = lane >> 4; k < np; k += 2) ms += E[k * 16 + pp].w;
         ms += __shfl_down_sync(FULL, ms, 16);
         if (lane < 16) msum[lane] = ms;
     }
@@ -204,18 +240,18 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         const int p = pixel_of(i < total ? i : total - 1);
         if (i < total) {
             const int base = pbase[p], np = pcnt[p];
-            const float4 Kq = E[i];
-            const float4* Jp = E + base;
+            const float4 Kq = E[(i - base) * 16 + p];
+            const float4* Jp = E + p;  // entry j of pixel p: Jp[16 j]
             float A0 = 0.0f, A1 = 0.0f;
             int j = 0;
             for (; j + 3 < np; j += 4) {
-                const float4 J0 = Jp[j], J1 = Jp[j + 1], J2 = Jp[j + 2], J3 = Jp[j + 3];
+                const float4 J0 = Jp[16 * j], J1 = Jp[16 * (j + 1)], J2 = Jp[16 * (j + 2)], J3 = Jp[16 * (j + 3)];
                 pair(Kq, J0, A0);
                 pair(Kq, J1, A1);
                 pair(Kq, J2, A0);
                 pair(Kq, J3, A1);
             }
-            for (; j < np; ++j) pair(Kq, Jp[j], A0);
+            for (; j < np; ++j) pair(Kq, Jp[16 * j], A0);
             Wst[p * L + (i - base)] = ex2_approx(ntl * (msum[p] + (A0 + A1))) * (2.0f * Kq.w);
         }
     }
