@@ -34,6 +34,11 @@ constexpr int kChainStep = VOGE_CHAIN_STEP;
 #define VOGE_SETUP_STEP 2
 #endif
 constexpr int kSetupStep = VOGE_SETUP_STEP;
+// Matching lane pairs a warp needs before it aggregates its reductions.
+#ifndef VOGE_AGG_PAIRS
+#define VOGE_AGG_PAIRS 4
+#endif
+constexpr int kAggPairs = VOGE_AGG_PAIRS;
 
 // How a tile adds the attribute gradient dL/dc_g += W_k dL/dI:
 //   kAttrLane:  one reduction per lane and channel (4 <= C < 8),
@@ -508,14 +513,25 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
         if (C > 1) gi1 = __ldg(gp + 1);
         if (C > 2) gi2 = __ldg(gp + 2);
     }
-    // kChainStep entries at a time: their records and second records
-    for (int e0 = 0; e0 < n; e0 += kChainStep) {
+    // kChainStep entries at a time: their records and second records.  The
+    // packed form runs the loop over the warp's longest list, so that the
+    // whole warp can aggregate its reductions: lanes 2i and 2i + 1 are
+    // horizontally adjacent pixels, which often keep the same Gaussian at the
+    // same list position.  When at least kAggPairs such pairs do, lane 2i adds
+    // lane 2i + 1's twelve sums to its own and only lane 2i issues the three
+    // reductions (the twelve shuffles cost about what four pairs' reductions
+    // save).  Past the end of its list a lane computes on record 0 and issues
+    // nothing.
+    const int nloop = packed ? (int)__reduce_max_sync(0xffffffffu, (unsigned)n) : n;
+    for (int e0 = 0; e0 < nloop; e0 += kChainStep) {
         float4 J[kChainStep];
         int64_t o[kChainStep];
+        int32_t gk[kChainStep];
 #pragma unroll
         for (int h = 0; h < kChainStep; ++h) {
-            J[h] = jst[min(e0 + h, n - 1) * NT + tid];
-            o[h] = vb + VOGE_IDX(a.hdr, __float_as_int(J[h].w), N, kChkRecord);
+            J[h] = jst[max(min(e0 + h, n - 1), 0) * NT + tid];
+            gk[h] = e0 + h < n ? (int32_t)VOGE_IDX(a.hdr, __float_as_int(J[h].w), N, kChkRecord) : 0;
+            o[h] = vb + gk[h];
         }
         float4 r[kChainStep][4], q[kChainStep][2];
         float wk[kChainStep];
@@ -524,21 +540,37 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
             load_rec(a.ws.rec, o[h], r[h][0], r[h][1], r[h][2], r[h][3]);
             q[h][0] = __ldg(a.ws.rec2 + 2 * o[h]);
             q[h][1] = __ldg(a.ws.rec2 + 2 * o[h] + 1);
-            const int e = min(e0 + h, n - 1);
+            const int e = max(min(e0 + h, n - 1), 0);
             wk[h] = kChain ? (wi ? __ldg(wi + e) : swk[e * NT + tid]) : 0.0f;
         }
 #pragma unroll
         for (int h = 0; h < kChainStep; ++h) {
-            const int e = e0 + h;
-            if (e < n) {
-                const Trace tr = trace_px(r[h][0], r[h][1], r[h][2], r[h][3], px, py);
-                float gv[9];
-                chain_to_camera(q[h][0], q[h][1], tr, r[h][3], invF, J[h].x, J[h].y, J[h].z, gv);
+            const bool live = e0 + h < n;
+            float gv[12];
+            const Trace tr = trace_px(r[h][0], r[h][1], r[h][2], r[h][3], px, py);
+            chain_to_camera(q[h][0], q[h][1], tr, r[h][3], invF, J[h].x, J[h].y, J[h].z, gv);
+            gv[9] = kChain ? wk[h] * gi0 : 0.0f;
+            gv[10] = kChain ? wk[h] * gi1 : 0.0f;
+            gv[11] = kChain ? wk[h] * gi2 : 0.0f;
+            bool issue = live;
+            if constexpr (packed) {
+                const int key = live ? gk[h] : -1 - lane;
+                const bool odd = (lane & 1) != 0;
+                const bool pair = __shfl_xor_sync(0xffffffffu, key, 1) == key;
+                if (__popc(__ballot_sync(0xffffffffu, pair && !odd)) >= kAggPairs) {
+#pragma unroll
+                    for (int x = 0; x < 12; ++x) {
+                        const float t = __shfl_down_sync(0xffffffffu, gv[x], 1);
+                        if (pair && !odd) gv[x] += t;
+                    }
+                    issue = live && !(pair && odd);
+                }
+            }
+            if (issue) {
                 float* gc = a.ws.gcam + kGcamStride * o[h];
                 red_add_v4(gc, gv[0], gv[1], gv[2], gv[3]);
                 red_add_v4(gc + 4, gv[4], gv[5], gv[6], gv[7]);
-                if (kChain) red_add_v4(gc + 8, gv[8], wk[h] * gi0, wk[h] * gi1, wk[h] * gi2);
-                else red_add_v4(gc + 8, gv[8], 0.0f, 0.0f, 0.0f);
+                red_add_v4(gc + 8, gv[8], gv[9], gv[10], gv[11]);
             }
         }
     }
