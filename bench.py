@@ -787,37 +787,72 @@ def main():
     # ------------------------------------------------ e2e through host buffers
     # The same step as the timed one (forward, MSE, backward, Adam) through the
     # public API, with the parameters and targets copied in from pinned host
-    # memory and the loss and updated parameters copied back, every step.
+    # memory and the loss and updated parameters copied back, every step.  The
+    # inputs of step i + 1 are copied on a second stream, into the other of
+    # two buffer sets, while step i runs (a data loader's prefetch); step i's
+    # results are copied out after it and the host waits for them.
     e2e = None
     if not args.no_e2e:
         h_par = torch.tensor(host_par).pin_memory()
         h_target = target.cpu().pin_memory()
         h_out = torch.empty(n_par).pin_memory()
         h_loss = torch.empty(1).pin_memory()
+        pars = [torch.empty_like(par), torch.empty_like(par)]
+        targets = [torch.empty_like(target), torch.empty_like(target)]
+        cstream = torch.cuda.Stream(device=dev)
+        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        main = torch.cuda.current_stream()
 
-        def e2e_step():
-            par.copy_(h_par, non_blocking=True)
-            target.copy_(h_target, non_blocking=True)
-            step()
-            h_out.copy_(par, non_blocking=True)
-            h_loss.copy_(loss, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            return float(h_loss[0])
+        def make_step(pb, tb):
+            mb, pvb, ab = views(pb)
 
-        for _ in range(args.warmup):
-            e2e_step()
+            def st():
+                r.forward(mb, pvb, ab, out=(image, weights, index))
+                loss.zero_()
+                voge.voge_mse_grad(image, tb, g_image, loss)
+                r.backward(mb, pvb, ab, index, g_image, g_means, g_inv_cov, g_attr, g_cam, reuse_projection=True,
+                           weights=weights)
+                step_no[0] += 1
+                voge.voge_adam_step(pb, grad, m_adam, v_adam, lr=1e-4, step=step_no[0])
+            return st
+
+        steps_e2e = [make_step(pars[0], targets[0]), make_step(pars[1], targets[1])]
+
+        def copy_in(b):
+            # buffer set b was last used by the step before the previous one,
+            # which the host has waited for
+            with torch.cuda.stream(cstream):
+                pars[b].copy_(h_par, non_blocking=True)
+                targets[b].copy_(h_target, non_blocking=True)
+                ev_in[b].record(cstream)
+
+        def e2e_run(k):
+            copy_in(0)
+            for i in range(k):
+                b = i & 1
+                if i + 1 < k:
+                    copy_in(b ^ 1)
+                main.wait_event(ev_in[b])
+                steps_e2e[b]()
+                h_out.copy_(pars[b], non_blocking=True)
+                h_loss.copy_(loss, non_blocking=True)
+                main.synchronize()
+                float(h_loss[0])
+
+        e2e_run(args.warmup)
+        torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         t_e2e, _ = reduce_over_ranks(time.perf_counter() - t0, 0, world, dev)
         e2e = {"value": pix_all / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (n_par + target.numel())),
                "d2h_bytes_per_step": int(4 * (n_par + 1)),
                "ms_per_step": 1e3 * t_e2e / args.steps,
-               "what": "forward + MSE + backward + Adam as the timed step; parameters and targets in, loss and "
-                       "updated parameters out, synchronised every step"}
+               "what": "forward + MSE + backward + Adam as the timed step; parameters and targets in (the next "
+                       "step's copied on a second stream during the current step), loss and updated parameters "
+                       "out, the host waiting for each step's results"}
 
     # ------------------------------------------------ plain comparator
     plain = None
