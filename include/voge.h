@@ -43,7 +43,7 @@ enum {
     VOGE_ERR_ARG = -1,        /* a size, pointer or parameter is invalid */
     VOGE_ERR_WORKSPACE = -2,  /* workspace NULL or smaller than voge_workspace_bytes() */
     VOGE_ERR_CUDA = -3,       /* a CUDA call or kernel launch failed */
-    VOGE_ERR_UNSUPPORTED = -4,/* a combination this build does not implement */
+    VOGE_ERR_UNSUPPORTED = -4,/* a combination the library does not implement */
     VOGE_ERR_TIMEOUT = -5,    /* a bounded wait ran out (serving) */
     VOGE_ERR_ADMISSION = -6,  /* request larger than the server's memory budget */
     VOGE_ERR_BUSY = -7,       /* no free slot / queue full (serving) */
