@@ -227,6 +227,8 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
             if (lane >= d) incl += t;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cnt;
+        // every row full (all 32 pixels keep L entries): entry i is (i / 32, i % 32)
+        const bool rows_full = total == 32 * K;
         for (int i0 = 0; i0 < total; i0 += 32 * kSetupStep) {
             int pp[kSetupStep], kk[kSetupStep];
             int32_t gg[kSetupStep];
@@ -234,22 +236,26 @@ __device__ __forceinline__ void backward_tile(const Args& a, int t, int hb, int 
 #pragma unroll
             for (int h = 0; h < kSetupStep; ++h) {
                 const int i = min(i0 + 32 * h + lane, total - 1);
-                int k = 0;  // the last row whose first entry is at or before i
+                int k = i >> 5, p = i & 31;
+                if (!rows_full) {
+                    k = 0;  // the last row whose first entry is at or before i
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int b = __shfl_sync(0xffffffffu, excl, k + step);
-                    if (k + step < KM && b <= i) k += step;
-                }
-                // the (i - first)-th set bit of M_k, by halving popcounts
-                unsigned m = __shfl_sync(0xffffffffu, mrow, k);
-                int r = i - __shfl_sync(0xffffffffu, excl, k), p = 0;
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int b = __shfl_sync(0xffffffffu, excl, k + step);
+                        if (k + step < KM && b <= i) k += step;
+                    }
+                    // the (i - first)-th set bit of M_k, by halving popcounts
+                    unsigned m = __shfl_sync(0xffffffffu, mrow, k);
+                    int r = i - __shfl_sync(0xffffffffu, excl, k);
+                    p = 0;
 #pragma unroll
-                for (int w = 16; w >= 1; w >>= 1) {
-                    const int c = __popc(m & ((1u << w) - 1u));
-                    if (r >= c) {
-                        r -= c;
-                        m >>= w;
-                        p += w;
+                    for (int w = 16; w >= 1; w >>= 1) {
+                        const int c = __popc(m & ((1u << w) - 1u));
+                        if (r >= c) {
+                            r -= c;
+                            m >>= w;
+                            p += w;
+                        }
                     }
                 }
                 pp[h] = p;

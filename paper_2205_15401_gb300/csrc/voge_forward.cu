@@ -180,27 +180,33 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         if (lane >= d) rincl += t;
     }
     const int rexcl = rincl - crow;
+    // every row full (all 16 pixels keep L entries): entry i is (i / 16, i % 16)
+    const bool rows_full = total == 16 * L;
     for (int i0 = 0; i0 < total; i0 += 64) {
         float4 r[2][4];
         int pp[2], kk[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int i = min(i0 + 32 * h + lane, total - 1);
-            int k = 0;  // the last row whose first entry is at or before i
+            int k = i >> 4, p = i & 15;
+            if (!rows_full) {
+                k = 0;  // the last row whose first entry is at or before i
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int b = __shfl_sync(FULL, rexcl, k + step);
-                if (k + step < KM && b <= i) k += step;
-            }
-            unsigned m = __shfl_sync(FULL, mrow, k);
-            int rr = i - __shfl_sync(FULL, rexcl, k), p = 0;  // the rr-th set bit of M_k
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int b = __shfl_sync(FULL, rexcl, k + step);
+                    if (k + step < KM && b <= i) k += step;
+                }
+                unsigned m = __shfl_sync(FULL, mrow, k);
+                int rr = i - __shfl_sync(FULL, rexcl, k);  // the rr-th set bit of M_k
+                p = 0;
 #pragma unroll
-            for (int w = 8; w >= 1; w >>= 1) {
-                const int c = __popc(m & ((1u << w) - 1u));
-                if (rr >= c) {
-                    rr -= c;
-                    m >>= w;
-                    p += w;
+                for (int w = 8; w >= 1; w >>= 1) {
+                    const int c = __popc(m & ((1u << w) - 1u));
+                    if (rr >= c) {
+                        rr -= c;
+                        m >>= w;
+                        p += w;
+                    }
                 }
             }
             pp[h] = p;
