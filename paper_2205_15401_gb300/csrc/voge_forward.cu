@@ -241,11 +241,14 @@ __device__ __forceinline__ void fine_segment(const Args& a, const ViewDesc& vd, 
         const float u = ((Kq.x - J.x) + (Kq.y - J.y)) * J.z;
         A = fmaf(copysignf(J.w, u), 1.0f - erfc_as28(fabsf(u)), A);
     };
+    // with every list full, pixel i / L (a multiply and a shift: exact for
+    // i < 32 L <= 1024 and L <= 32) replaces the search over the bases
+    const int div_mul = (65536 + L - 1) / L;
     for (int i0 = 0; i0 < total; i0 += 32) {
         const int i = i0 + lane;
-        const int p = pixel_of(i < total ? i : total - 1);
+        const int p = rows_full ? (min(i, total - 1) * div_mul) >> 16 : pixel_of(i < total ? i : total - 1);
         if (i < total) {
-            const int base = pbase[p], np = pcnt[p];
+            const int base = rows_full ? p * L : pbase[p], np = rows_full ? L : pcnt[p];
             const float4 Kq = E[(i - base) * 16 + p];
             const float4* Jp = E + p;  // entry j of pixel p: Jp[16 j]
             float A0 = 0.0f, A1 = 0.0f;
