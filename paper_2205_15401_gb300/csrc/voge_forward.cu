@@ -600,8 +600,11 @@ __device__ __forceinline__ void render_tile(const Args& a, int t) {
         const int irow = ty * TH + 2 * warp + rw;
         const int colb = 32 * warp + 16 * rw;  // sli column of the segment's pixel 0
         const int np_lane = __shfl_sync(0xffffffffu, n, 16 * rw + (lane & 15));
-        if (lane < 16)
-            for (int k = 0; k < L; ++k) istg[lane * L + k] = k < np_lane ? sli[k * NT + colb + lane] : -1;
+        {
+            // two lanes per pixel (even and odd list positions)
+            const int pp = lane & 15;
+            for (int k = lane >> 4; k < L; k += 2) istg[pp * L + k] = k < np_lane ? sli[k * NT + colb + pp] : -1;
+        }
         __syncwarp();
         if (irow < H) {
             const int64_t o0 = ((int64_t)irow * W + tx * kTileW) * L;
