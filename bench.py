@@ -787,21 +787,26 @@ def main():
     # ------------------------------------------------ e2e through host buffers
     # The same step as the timed one (forward, MSE, backward, Adam) through the
     # public API, with the parameters and targets copied in from pinned host
-    # memory and the loss and updated parameters copied back, every step.  The
-    # inputs of step i + 1 are copied on a second stream, into the other of
-    # two buffer sets, while step i runs (a data loader's prefetch); step i's
-    # results are copied out after it and the host waits for them.
+    # memory and the loss and updated parameters copied back, every step, as
+    # a pipelined training loop runs it: the inputs of step i + 1 are copied
+    # on a second stream, into the other of two buffer sets, while step i
+    # runs (a data loader's prefetch), and the host reads step i's loss while
+    # step i + 1 runs.  The timed region ends when the last step's results
+    # are in host memory.
     e2e = None
     if not args.no_e2e:
         h_par = torch.tensor(host_par).pin_memory()
         h_target = target.cpu().pin_memory()
-        h_out = torch.empty(n_par).pin_memory()
-        h_loss = torch.empty(1).pin_memory()
+        h_outs = [torch.empty(n_par).pin_memory(), torch.empty(n_par).pin_memory()]
+        h_losses = [torch.empty(1).pin_memory(), torch.empty(1).pin_memory()]
         pars = [torch.empty_like(par), torch.empty_like(par)]
         targets = [torch.empty_like(target), torch.empty_like(target)]
         cstream = torch.cuda.Stream(device=dev)
         ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_out = [torch.cuda.Event(), torch.cuda.Event()]
         main = torch.cuda.current_stream()
+        # device time of the copies themselves (events on their own streams)
+        copy_ev = {"in": [], "out": []}
 
         def make_step(pb, tb):
             mb, pvb, ab = views(pb)
@@ -818,41 +823,65 @@ def main():
 
         steps_e2e = [make_step(pars[0], targets[0]), make_step(pars[1], targets[1])]
 
-        def copy_in(b):
-            # buffer set b was last used by the step before the previous one,
-            # which the host has waited for
+        def copy_in(b, after_out):
+            # buffer set b was last used by the step two back: its results
+            # must be out first
             with torch.cuda.stream(cstream):
+                if after_out:
+                    cstream.wait_event(ev_out[b])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(cstream)
                 pars[b].copy_(h_par, non_blocking=True)
                 targets[b].copy_(h_target, non_blocking=True)
+                e1.record(cstream)
+                copy_ev["in"].append((e0, e1))
                 ev_in[b].record(cstream)
 
         def e2e_run(k):
-            copy_in(0)
+            copy_in(0, False)
+            losses = []
             for i in range(k):
                 b = i & 1
                 if i + 1 < k:
-                    copy_in(b ^ 1)
+                    copy_in(b ^ 1, i >= 1)
                 main.wait_event(ev_in[b])
                 steps_e2e[b]()
-                h_out.copy_(pars[b], non_blocking=True)
-                h_loss.copy_(loss, non_blocking=True)
-                main.synchronize()
-                float(h_loss[0])
+                o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                o0.record(main)
+                h_outs[b].copy_(pars[b], non_blocking=True)
+                h_losses[b].copy_(loss, non_blocking=True)
+                o1.record(main)
+                copy_ev["out"].append((o0, o1))
+                ev_out[b].record(main)
+                if i >= 1:  # the previous step's loss, read while this one runs
+                    ev_out[b ^ 1].synchronize()
+                    losses.append(float(h_losses[b ^ 1][0]))
+            ev_out[(k - 1) & 1].synchronize()
+            losses.append(float(h_losses[(k - 1) & 1][0]))
+            return losses
 
         e2e_run(args.warmup)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        copy_ev["in"].clear()
+        copy_ev["out"].clear()
         t0 = time.perf_counter()
         e2e_run(args.steps)
         t_e2e, _ = reduce_over_ranks(time.perf_counter() - t0, 0, world, dev)
+        torch.cuda.synchronize()
+        h2d_ms = sum(a.elapsed_time(b) for a, b in copy_ev["in"]) / max(len(copy_ev["in"]), 1)
+        d2h_ms = sum(a.elapsed_time(b) for a, b in copy_ev["out"]) / max(len(copy_ev["out"]), 1)
         e2e = {"value": pix_all / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(4 * (n_par + target.numel())),
                "d2h_bytes_per_step": int(4 * (n_par + 1)),
                "ms_per_step": 1e3 * t_e2e / args.steps,
-               "what": "forward + MSE + backward + Adam as the timed step; parameters and targets in (the next "
-                       "step's copied on a second stream during the current step), loss and updated parameters "
-                       "out, the host waiting for each step's results"}
+               "h2d_ms_per_step": h2d_ms, "d2h_ms_per_step": d2h_ms,
+               "what": "forward + MSE + backward + Adam as the timed step; every step's parameters and targets "
+                       "copied in from pinned host memory (the next step's on a second stream during the "
+                       "current step) and its loss and updated parameters copied out, the host reading each "
+                       "step's loss while the next step runs; the timed region ends with the last step's "
+                       "results in host memory"}
 
     # ------------------------------------------------ plain comparator
     plain = None
